@@ -1,0 +1,457 @@
+// C ABI of the CP-APR MU library: argument checks, context lifecycle, model
+// I/O and the one-off Phi / MTTKRP / log-likelihood calls.  The MU loop
+// itself lives in solver.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+thread_local std::string g_create_error = "no error";
+}
+
+namespace cpapr {
+
+cpapr_status fail(cpapr_ctx *ctx, cpapr_status st, const std::string &msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, CPAPR_E_NOMEM, msg);
+    }
+    if (ctx) ctx->sticky = true;
+    return fail(ctx, CPAPR_E_CUDA, msg);
+}
+
+cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocs.push_back(*p);
+    ctx->device_bytes += (int64_t)bytes;
+    return CPAPR_OK;
+}
+
+ProfScope::ProfScope(cpapr_ctx *c, int k) : ctx(c), kind(k) {
+    if (!ctx->opt.profile) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    auto take = [&]() {
+        cudaEvent_t e = nullptr;
+        if (!ctx->ev_pool.empty()) {
+            e = ctx->ev_pool.back();
+            ctx->ev_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    };
+    a = take();
+    b = take();
+    if (a && b) cudaEventRecord(a, ctx->stream);
+}
+
+ProfScope::~ProfScope() {
+    if (!a || !b) {
+        if (a) ctx->ev_pool.push_back(a);
+        if (b) ctx->ev_pool.push_back(b);
+        return;
+    }
+    cudaEventRecord(b, ctx->stream);
+    ctx->ev_pending.push_back({kind, {a, b}});
+}
+
+void prof_collect(cpapr_ctx *ctx) {
+    for (auto &p : ctx->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.second.second) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            ctx->prof_launches[p.first] += 1;
+            ctx->prof_ms[p.first] += ms;
+        }
+        ctx->ev_pool.push_back(p.second.first);
+        ctx->ev_pool.push_back(p.second.second);
+    }
+    ctx->ev_pending.clear();
+}
+
+static int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Built-in choice of lanes per nonzero and nonzeros per tile.
+// FP64: one lane per nonzero up to 16 ranks (no redundant division or
+// shuffle adds on the scarce FP64 pipe); FP32: 16-byte vectors of 4 ranks
+// per lane up to 32 ranks, 8 ranks per lane above.
+static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
+    const int Rp = ctx->Rp;
+    int g;
+    if (ctx->esize == 8)
+        g = std::max(1, Rp / 16);
+    else
+        g = Rp <= 32 ? std::max(1, Rp / 4) : Rp / 8;
+    *lanes = g;
+    *tile = ctx->esize == 8 ? 2048 : 4096;
+    *reduction = CPAPR_REDUCE_SEGMENTED;
+    (void)n;
+}
+
+cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int reduction) {
+    if (!phi_config_supported((int)ctx->esize, ctx->N - 1, ctx->Rp, lanes))
+        return fail(ctx, CPAPR_E_ARG, "rank_lanes not supported for this rank and precision");
+    if (tile < 64 || tile > (1 << 20)) return fail(ctx, CPAPR_E_ARG, "tile_nnz must lie in [64, 2^20]");
+    ModeLayout &L = ctx->mode[n];
+    L.lanes = lanes;
+    L.reduction = reduction == CPAPR_REDUCE_ATOMIC ? CPAPR_REDUCE_ATOMIC : CPAPR_REDUCE_SEGMENTED;
+    if (L.tile_nnz != tile || !L.row_first) CPAPR_TRY(build_tiles(ctx, n, tile));
+    // per-tile log-likelihood partials (mode 0)
+    if (n == 0) {
+        if (ctx->llpart) cudaFreeAsync(ctx->llpart, ctx->stream);
+        ctx->llpart = nullptr;
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&ctx->llpart, (size_t)std::max(L.ntiles, 1) * 8, ctx->stream));
+    }
+    if (ctx->graph_exec[n]) {
+        cudaGraphExecDestroy(ctx->graph_exec[n]);
+        ctx->graph_exec[n] = nullptr;
+    }
+    return CPAPR_OK;
+}
+
+cpapr_status autotune(cpapr_ctx *ctx);
+
+}  // namespace cpapr
+
+using namespace cpapr;
+
+extern "C" {
+
+void cpapr_default_options(cpapr_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = CPAPR_FP64;
+    opt->reduction = CPAPR_REDUCE_AUTO;
+    opt->eps = 1e-10;
+    opt->kappa = 0.01;
+    opt->kappa_tol = 1e-10;
+    opt->seed = 0;
+    opt->stream = nullptr;
+    opt->tile_nnz = 0;
+    opt->rank_lanes = 0;
+    opt->use_graph = 1;
+    opt->autotune = 0;
+    opt->profile = 0;
+}
+
+const char *cpapr_version(void) { return "cpapr-gb300 0.1 (sm_103a)"; }
+
+const char *cpapr_last_error(const cpapr_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.empty() ? "no error" : ctx->err.c_str();
+}
+
+void cpapr_destroy(cpapr_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int n = 0; n < ctx->N; ++n) {
+        ModeLayout &L = ctx->mode[n];
+        if (L.row_first) cudaFree(L.row_first);
+        if (L.row_lo) cudaFree(L.row_lo);
+        if (L.split) cudaFree(L.split);
+        if (ctx->graph_exec[n]) cudaGraphExecDestroy(ctx->graph_exec[n]);
+    }
+    if (ctx->carry) cudaFree(ctx->carry);
+    if (ctx->llpart) cudaFree(ctx->llpart);
+    for (void *p : ctx->allocs) cudaFree(p);
+    for (auto &p : ctx->ev_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, const int64_t *const *idx,
+                          const double *vals, int32_t rank, const cpapr_options *opt, cpapr_ctx **out) {
+    if (!out) return fail(nullptr, CPAPR_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (nmodes < 2 || nmodes > CPAPR_MAX_MODES) return fail(nullptr, CPAPR_E_ARG, "nmodes must lie in [2, 8]");
+    if (!dims) return fail(nullptr, CPAPR_E_ARG, "dims is NULL");
+    for (int m = 0; m < nmodes; ++m)
+        if (dims[m] < 1 || dims[m] > INT32_MAX - 1) return fail(nullptr, CPAPR_E_RANGE, "each dim must lie in [1, 2^31-2]");
+    if (nnz < 0 || nnz > INT32_MAX - 4096) return fail(nullptr, CPAPR_E_RANGE, "nnz must lie in [0, 2^31 - 4096]");
+    if (nnz > 0 && (!idx || !vals)) return fail(nullptr, CPAPR_E_ARG, "idx or vals is NULL");
+    if (nnz > 0)
+        for (int m = 0; m < nmodes; ++m)
+            if (!idx[m]) return fail(nullptr, CPAPR_E_ARG, "idx[m] is NULL");
+    if (rank < 1 || rank > 128) return fail(nullptr, CPAPR_E_ARG, "rank must lie in [1, 128]");
+    cpapr_options o;
+    cpapr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != CPAPR_FP64 && o.precision != CPAPR_FP32) return fail(nullptr, CPAPR_E_ARG, "bad precision");
+    if (o.reduction < 0 || o.reduction > 2) return fail(nullptr, CPAPR_E_ARG, "bad reduction");
+    if (!(o.eps > 0.0) || !(o.kappa >= 0.0) || !(o.kappa_tol >= 0.0)) return fail(nullptr, CPAPR_E_ARG, "bad eps/kappa");
+    if (o.rank_lanes < 0 || o.rank_lanes > 32 || (o.rank_lanes & (o.rank_lanes - 1)))
+        return fail(nullptr, CPAPR_E_ARG, "rank_lanes must be 0 or a power of two <= 32");
+    if (o.tile_nnz != 0 && (o.tile_nnz < 64 || o.tile_nnz > (1 << 20)))
+        return fail(nullptr, CPAPR_E_ARG, "tile_nnz must be 0 or lie in [64, 2^20]");
+
+    cpapr_ctx *ctx = new (std::nothrow) cpapr_ctx();
+    if (!ctx) return fail(nullptr, CPAPR_E_NOMEM, "host allocation failed");
+    auto bail = [&](cpapr_status st) {
+        g_create_error = ctx->err;
+        cpapr_destroy(ctx);
+        return st;
+    };
+    ctx->N = nmodes;
+    ctx->nnz = nnz;
+    ctx->R = rank;
+    ctx->opt = o;
+    ctx->esize = o.precision == CPAPR_FP64 ? 8 : 4;
+    ctx->Rp = std::max(ctx->esize == 8 ? 2 : 4, next_pow2(rank));
+    for (int m = 0; m < nmodes; ++m) {
+        ctx->dims[m] = dims[m];
+        ctx->Imax = (int)std::max<int64_t>(ctx->Imax, dims[m]);
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGetDevice"));
+    if (o.stream) {
+        ctx->stream = (cudaStream_t)o.stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaStreamCreate"));
+        ctx->own_stream = true;
+    }
+    const int Rp = ctx->Rp;
+    void *p = nullptr;
+    cpapr_status st;
+#define CR_TRY(expr)                     \
+    do {                                 \
+        st = (expr);                     \
+        if (st != CPAPR_OK) return bail(st); \
+    } while (0)
+    CR_TRY(dev_alloc(ctx, &p, 64));
+    ctx->errflag = (int32_t *)p;
+    CR_TRY(dev_alloc(ctx, &p, sizeof(InnerState) * nmodes));
+    ctx->inner = (InnerState *)p;
+    CR_TRY(dev_alloc(ctx, &p, (size_t)Rp * 8));
+    ctx->lambda = (double *)p;
+    CR_TRY(dev_alloc(ctx, &p, (size_t)kColParts * Rp * 8));
+    ctx->colpart = (double *)p;
+    CR_TRY(dev_alloc(ctx, &p, (size_t)nmodes * Rp * 8));
+    ctx->colsum = (double *)p;
+    CR_TRY(dev_alloc(ctx, &p, 64 * 8));
+    ctx->scalars = (double *)p;
+    if (cudaMemsetAsync(ctx->inner, 0, sizeof(InnerState) * nmodes, ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, CPAPR_E_CUDA, "memset"));
+
+    CR_TRY(build_layouts(ctx, idx, vals));
+
+    for (int m = 0; m < nmodes; ++m) {
+        CR_TRY(dev_alloc(ctx, &p, (size_t)dims[m] * Rp * ctx->esize));
+        ctx->A[m] = p;
+        CR_TRY(dev_alloc(ctx, &p, (size_t)dims[m] * Rp * ctx->esize));
+        ctx->Phi[m] = p;
+        if (cudaMemsetAsync(ctx->A[m], 0, (size_t)dims[m] * Rp * ctx->esize, ctx->stream) != cudaSuccess ||
+            cudaMemsetAsync(ctx->Phi[m], 0, (size_t)dims[m] * Rp * ctx->esize, ctx->stream) != cudaSuccess)
+            return bail(fail(ctx, CPAPR_E_CUDA, "memset"));
+    }
+    CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * ctx->esize));
+    ctx->B = p;
+    CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * ctx->esize));
+    ctx->outbuf = p;
+    CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * 8));
+    ctx->stage = (double *)p;
+
+    for (int n = 0; n < nmodes; ++n) {
+        int lanes, tile, red;
+        heuristic_config(ctx, n, &lanes, &tile, &red);
+        if (o.rank_lanes) lanes = o.rank_lanes;
+        if (o.tile_nnz) tile = o.tile_nnz;
+        if (o.reduction) red = o.reduction;
+        CR_TRY(configure_mode(ctx, n, lanes, tile, red));
+    }
+    if (o.autotune) CR_TRY(autotune(ctx));
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build"));
+#undef CR_TRY
+    *out = ctx;
+    return CPAPR_OK;
+}
+
+#define API_ENTER(ctx)                                                             \
+    do {                                                                           \
+        if (!(ctx)) return fail(nullptr, CPAPR_E_ARG, "ctx is NULL");             \
+        if ((ctx)->sticky) return CPAPR_E_CUDA;                                    \
+    } while (0)
+
+cpapr_status cpapr_set_model(cpapr_ctx *ctx, const double *lambda, const double *const *factors) {
+    API_ENTER(ctx);
+    if (!lambda || !factors) return fail(ctx, CPAPR_E_ARG, "lambda or factors is NULL");
+    for (int m = 0; m < ctx->N; ++m)
+        if (!factors[m]) return fail(ctx, CPAPR_E_ARG, "factors[m] is NULL");
+    std::vector<double> hl(ctx->Rp, 0.0);
+    CPAPR_CUDA(ctx, cudaMemcpy(hl.data(), lambda, (size_t)ctx->R * 8, cudaMemcpyDefault));
+    for (int r = 0; r < ctx->R; ++r)
+        if (!(hl[r] >= 0.0) || std::isinf(hl[r])) return fail(ctx, CPAPR_E_VALUE, "lambda must be finite and >= 0");
+    CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, 16, ctx->stream));
+    CPAPR_CUDA(ctx, cudaMemcpyAsync(ctx->lambda, hl.data(), (size_t)ctx->Rp * 8, cudaMemcpyHostToDevice, ctx->stream));
+    for (int m = 0; m < ctx->N; ++m) {
+        CPAPR_TRY(upload_matrix(ctx, factors[m], ctx->dims[m], ctx->A[m]));
+        CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->Phi[m], 0, (size_t)ctx->dims[m] * ctx->Rp * ctx->esize, ctx->stream));
+    }
+    int32_t flags[4] = {0, 0, 0, 0};
+    CPAPR_CUDA(ctx, cudaMemcpyAsync(flags, ctx->errflag, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->k_total = 0;
+    if (flags[2]) {
+        ctx->model_set = false;
+        return fail(ctx, CPAPR_E_VALUE, "factor entries must be finite and >= 0");
+    }
+    ctx->model_set = true;
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_init_random(cpapr_ctx *ctx, uint64_t seed) {
+    API_ENTER(ctx);
+    CPAPR_TRY(launch_init_random(ctx, seed));
+    for (int m = 0; m < ctx->N; ++m)
+        CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->Phi[m], 0, (size_t)ctx->dims[m] * ctx->Rp * ctx->esize, ctx->stream));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->k_total = 0;
+    ctx->model_set = true;
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_get_model(cpapr_ctx *ctx, double *lambda, double *const *factors) {
+    API_ENTER(ctx);
+    if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
+    if (lambda) CPAPR_CUDA(ctx, cudaMemcpyAsync(lambda, ctx->lambda, (size_t)ctx->R * 8, cudaMemcpyDefault, ctx->stream));
+    if (factors)
+        for (int m = 0; m < ctx->N; ++m) {
+            if (!factors[m]) continue;
+            CPAPR_TRY(download_matrix(ctx, ctx->A[m], ctx->dims[m], factors[m]));
+            // download_matrix stages FP32 through ctx->stage: finish before reuse
+            CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CPAPR_OK;
+}
+
+static cpapr_status check_mode(cpapr_ctx *ctx, int32_t mode) {
+    if (mode < 0 || mode >= ctx->N) return fail(ctx, CPAPR_E_ARG, "mode out of range");
+    if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *out) {
+    API_ENTER(ctx);
+    CPAPR_TRY(check_mode(ctx, mode));
+    if (!out) return fail(ctx, CPAPR_E_ARG, "out is NULL");
+    if (B) {
+        CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, 16, ctx->stream));
+        CPAPR_TRY(upload_matrix(ctx, B, ctx->dims[mode], ctx->B));
+    } else {
+        CPAPR_TRY(launch_scale_b(ctx, mode, ctx->B));
+    }
+    // Phi[mode] holds the previous iteration's Phi that S reads: compute into
+    // the separate output buffer instead.
+    CPAPR_TRY(launch_phi(ctx, mode, OP_PHI, ctx->B, ctx->outbuf, nullptr));
+    CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_mttkrp(cpapr_ctx *ctx, int32_t mode, double *out) {
+    API_ENTER(ctx);
+    CPAPR_TRY(check_mode(ctx, mode));
+    if (!out) return fail(ctx, CPAPR_E_ARG, "out is NULL");
+    CPAPR_TRY(launch_phi(ctx, mode, OP_MTTKRP, nullptr, ctx->outbuf, nullptr));
+    CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
+    API_ENTER(ctx);
+    if (!out) return fail(ctx, CPAPR_E_ARG, "out is NULL");
+    if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
+    CPAPR_TRY(launch_scale_b(ctx, 0, ctx->B));
+    CPAPR_TRY(launch_loglik(ctx, ctx->B, ctx->scalars));
+    CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
+    CPAPR_CUDA(ctx, cudaMemcpyAsync(out, ctx->scalars, 8, cudaMemcpyDefault, ctx->stream));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_mu_solve(cpapr_ctx *ctx, double tol, int32_t max_outer, int32_t max_inner, cpapr_result *res,
+                            int32_t *inner_trace, double *ll_trace) {
+    API_ENTER(ctx);
+    if (!res) return fail(ctx, CPAPR_E_ARG, "res is NULL");
+    if (max_outer < 0 || max_inner < 1 || !(tol >= 0.0)) return fail(ctx, CPAPR_E_ARG, "bad tol / iteration bounds");
+    if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
+    return mu_solve(ctx, tol, max_outer, max_inner, res, inner_trace, ll_trace);
+}
+
+cpapr_status cpapr_batch_mu_solve(cpapr_ctx *const *ctxs, int32_t count, double tol, int32_t max_outer,
+                                  int32_t max_inner, cpapr_result *results) {
+    if (!ctxs || !results || count < 0) return fail(nullptr, CPAPR_E_ARG, "bad batch arguments");
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return fail(nullptr, CPAPR_E_ARG, "ctxs[i] is NULL");
+        if (ctxs[i]->sticky) return CPAPR_E_CUDA;
+        if (!ctxs[i]->model_set) return fail(ctxs[i], CPAPR_E_STATE, "no model set");
+        if (ctxs[i]->esize != ctxs[0]->esize) return fail(nullptr, CPAPR_E_ARG, "mixed precisions in a batch");
+    }
+    if (max_outer < 0 || max_inner < 1 || !(tol >= 0.0)) return fail(nullptr, CPAPR_E_ARG, "bad tol / iteration bounds");
+    return batch_mu_solve(ctxs, count, tol, max_outer, max_inner, results);
+}
+
+cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info) {
+    if (!ctx || !info) return CPAPR_E_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->nmodes = ctx->N;
+    info->rank = ctx->R;
+    info->rank_padded = ctx->Rp;
+    info->precision = ctx->opt.precision;
+    info->nnz = ctx->nnz;
+    for (int m = 0; m < ctx->N; ++m) {
+        info->dims[m] = ctx->dims[m];
+        info->tile_nnz[m] = ctx->mode[m].tile_nnz;
+        info->rank_lanes[m] = ctx->mode[m].lanes;
+        info->reduction[m] = ctx->mode[m].reduction;
+        info->ntiles[m] = ctx->mode[m].ntiles;
+        info->nsplit[m] = ctx->mode[m].nsplit;
+    }
+    info->device_bytes = ctx->device_bytes;
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_kernel_stats(cpapr_ctx *ctx, int32_t kind, int64_t *launches, double *total_ms, int32_t reset) {
+    API_ENTER(ctx);
+    if (kind < 0 || kind >= K_NKINDS) return fail(ctx, CPAPR_E_ARG, "bad kernel kind");
+    prof_collect(ctx);
+    if (launches) *launches = ctx->prof_launches[kind];
+    if (total_ms) *total_ms = ctx->prof_ms[kind];
+    if (reset) {
+        ctx->prof_launches[kind] = 0;
+        ctx->prof_ms[kind] = 0.0;
+    }
+    return CPAPR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,514 @@
+// Index builder: COO -> one mode-sorted layout per mode.
+//
+// The paper's Section "CP-APR MU Implementation and Parallelization" sorts
+// the nonzeros once per mode at the start so that entries updating the same
+// row of Phi^(n) are contiguous, and keeps N permutation arrays.  Here the
+// permutation is applied once: each mode gets its own physically permuted
+// copy of the other modes' coordinates and of the values, so the hot loop
+// streams them contiguously instead of reading through a permutation array
+// (the paper notes that indirect access through the permutation is slow).
+//
+// Steps (all on the device):
+//   1. copy the int64 COO in, check 0 <= i_m < I_m and x finite and >= 0,
+//      narrow coordinates to int32;
+//   2. per mode n: stable LSD radix sort of (i_n, position) with 8-bit digits
+//      (per-tile digit histograms, an exclusive scan, and a stable scatter
+//      that ranks equal digits with warp match/ballot);
+//   3. seg[i] = first sorted position of row i (I_n + 1 offsets);
+//   4. gather the other modes' coordinates and the values in sorted order;
+//   5. tile tables: tiles of tile_nnz consecutive sorted nonzeros, the row
+//      holding each tile's first nonzero, the first row starting in each
+//      tile, and the list of rows that span more than one tile.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace cpapr {
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 (in place), three kernels + recursion on block sums
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total, uint32_t *sm_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? sm_warp[lane] : 0u;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sm_warp[lane] = s - w;
+        if (lane == nw - 1) sm_warp[32] = s;
+    }
+    __syncthreads();
+    uint32_t r = sm_warp[warp] + x - v;
+    *total = sm_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t *__restrict__ d, int64_t n, uint32_t *__restrict__ bsum) {
+    __shared__ uint32_t smw[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += d[base + k];
+    uint32_t tot;
+    block_exclusive_scan(s, &tot, smw);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void scan_apply_kernel(uint32_t *__restrict__ d, int64_t n, const uint32_t *__restrict__ boff,
+                                  uint32_t *__restrict__ total_out) {
+    __shared__ uint32_t smw[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? d[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t pre = block_exclusive_scan(s, &tot, smw) + (boff ? boff[blockIdx.x] : 0u);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) d[base + k] = pre;
+        pre += v[k];
+    }
+    if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *total_out = pre;
+}
+
+cpapr_status exclusive_scan_u32(cpapr_ctx *ctx, uint32_t *data, int64_t n, uint32_t *total_out_dev) {
+    if (n <= 0) {
+        if (total_out_dev) CPAPR_CUDA(ctx, cudaMemsetAsync(total_out_dev, 0, 4, ctx->stream));
+        return CPAPR_OK;
+    }
+    int64_t nb = ceil_div(n, kScanTile);
+    uint32_t *bs = nullptr;
+    if (nb > 1) {
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&bs, nb * 4, ctx->stream));
+        scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(data, n, bs);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        cpapr_status st = exclusive_scan_u32(ctx, bs, nb, nullptr);
+        if (st != CPAPR_OK) return st;
+    }
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(data, n, bs, total_out_dev);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    if (bs) CPAPR_CUDA(ctx, cudaFreeAsync(bs, ctx->stream));
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// input conversion and validation
+// ---------------------------------------------------------------------------
+__global__ void narrow_check_kernel(const int64_t *__restrict__ src, int64_t nnz, int64_t dim,
+                                    int32_t *__restrict__ dst, int32_t *__restrict__ errflag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = src[j];
+        if (v < 0 || v >= dim) {
+            atomicOr(&errflag[0], 1);
+            v = 0;
+        }
+        dst[j] = (int32_t)v;
+    }
+}
+
+__global__ void check_values_kernel(const double *__restrict__ v, int64_t nnz, int32_t *__restrict__ errflag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+        double x = v[j];
+        if (!(x >= 0.0) || isinf(x)) atomicOr(&errflag[1], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (uint32 key, uint32 value)
+// ---------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsRounds = 8;
+constexpr int kRsTile = kRsThreads * kRsRounds;
+
+__global__ void iota_kernel(uint32_t *__restrict__ v, int64_t n) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        v[j] = (uint32_t)j;
+}
+
+__global__ void rs_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *__restrict__ counts,
+                               int ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int k = threadIdx.x; k < kRsTile; k += kRsThreads) {
+        int64_t p = base + k;
+        if (p < n) atomicAdd(&h[(keys[p] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: elements of a tile are visited in position order, 256 at a
+// time; inside a round, equal digits are ranked by lane (match_any) and by
+// warp (per-warp counts turned into offsets), so the output keeps the input
+// order among equal digits.
+__global__ void rs_scatter_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                  uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+                                  const uint32_t *__restrict__ offsets, int ntiles) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[kRsThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offsets[(int64_t)tid * ntiles + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int q = 0; q < kRsRounds; ++q) {
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        int64_t p = base + (int64_t)q * kRsThreads + tid;
+        bool valid = p < n;
+        uint32_t key = valid ? kin[p] : 0u;
+        uint32_t val = valid ? vin[p] : 0u;
+        uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t r = run[tid];
+#pragma unroll
+            for (int w = 0; w < kRsThreads / 32; ++w) {
+                uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = r;
+                r += c;
+            }
+            run[tid] = r;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// Sorts keys/vals (n entries) by the low `bits` bits of the key, stably.
+// tmp buffers must hold n entries each.  Result ends in keys/vals.
+static cpapr_status radix_sort(cpapr_ctx *ctx, uint32_t *keys, uint32_t *vals, uint32_t *tk, uint32_t *tv,
+                               int64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return CPAPR_OK;
+    int ntiles = (int)ceil_div(n, kRsTile);
+    uint32_t *counts = nullptr;
+    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&counts, (size_t)256 * ntiles * 4, ctx->stream));
+    uint32_t *ka = keys, *va = vals, *kb = tk, *vb = tv;
+    int passes = (bits + 7) / 8;
+    for (int ps = 0; ps < passes; ++ps) {
+        int shift = ps * 8;
+        rs_hist_kernel<<<ntiles, kRsThreads, 0, ctx->stream>>>(ka, n, shift, counts, ntiles);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        CPAPR_TRY(exclusive_scan_u32(ctx, counts, (int64_t)256 * ntiles, nullptr));
+        rs_scatter_kernel<<<ntiles, kRsThreads, 0, ctx->stream>>>(ka, va, kb, vb, n, shift, counts, ntiles);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        CPAPR_CUDA(ctx, cudaMemcpyAsync(keys, ka, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        CPAPR_CUDA(ctx, cudaMemcpyAsync(vals, va, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    CPAPR_CUDA(ctx, cudaFreeAsync(counts, ctx->stream));
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// segment offsets and permuted copies
+// ---------------------------------------------------------------------------
+__global__ void seg_kernel(const uint32_t *__restrict__ skeys, int64_t nnz, int32_t In, int32_t *__restrict__ seg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t key = (int32_t)skeys[k];
+        int32_t prev = k > 0 ? (int32_t)skeys[k - 1] : -1;
+        for (int32_t r = prev + 1; r <= key; ++r) seg[r] = (int32_t)k;
+        if (k == nnz - 1)
+            for (int32_t r = key + 1; r <= In; ++r) seg[r] = (int32_t)nnz;
+    }
+}
+
+__global__ void gather_i32_kernel(const int32_t *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
+                                  int32_t *__restrict__ dst) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[perm[k]];
+}
+
+template <typename T>
+__global__ void gather_val_kernel(const double *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
+                                  T *__restrict__ dst) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = (T)src[perm[k]];
+}
+
+static unsigned grid_for(int64_t n, int threads = 256) {
+    int64_t g = ceil_div(n, threads);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const double *vals_in) {
+    const int N = ctx->N;
+    const int64_t nnz = ctx->nnz;
+    cudaStream_t s = ctx->stream;
+    // padded length so vector and bulk loads past the end stay inside the buffer
+    ctx->nnz_pad = ceil_div(std::max<int64_t>(nnz, 1), 256) * 256 + 256;
+    const int64_t np = ctx->nnz_pad;
+
+    int32_t *idx32[kMaxModes] = {};
+    double *vals = nullptr;
+    int64_t *stage = nullptr;
+    uint32_t *keys = nullptr, *perm = nullptr, *tk = nullptr, *tv = nullptr;
+    auto cleanup = [&]() {
+        for (int m = 0; m < N; ++m)
+            if (idx32[m]) cudaFreeAsync(idx32[m], s);
+        if (vals) cudaFreeAsync(vals, s);
+        if (stage) cudaFreeAsync(stage, s);
+        if (keys) cudaFreeAsync(keys, s);
+        if (perm) cudaFreeAsync(perm, s);
+        if (tk) cudaFreeAsync(tk, s);
+        if (tv) cudaFreeAsync(tv, s);
+    };
+#define BL_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) {                           \
+            cleanup();                                     \
+            return cuda_fail(ctx, _e, #call);              \
+        }                                                  \
+    } while (0)
+#define BL_TRY(expr)                   \
+    do {                               \
+        cpapr_status _st = (expr);     \
+        if (_st != CPAPR_OK) {         \
+            cleanup();                 \
+            return _st;                \
+        }                              \
+    } while (0)
+
+    const int64_t nb = std::max<int64_t>(nnz, 1);
+    BL_CUDA(cudaMemsetAsync(ctx->errflag, 0, 16, s));
+    BL_CUDA(cudaMallocAsync((void **)&stage, nb * 8, s));
+    BL_CUDA(cudaMallocAsync((void **)&vals, nb * 8, s));
+    for (int m = 0; m < N; ++m) {
+        BL_CUDA(cudaMallocAsync((void **)&idx32[m], nb * 4, s));
+        if (nnz > 0) {
+            BL_CUDA(cudaMemcpyAsync(stage, idx_in[m], nnz * 8, cudaMemcpyDefault, s));
+            narrow_check_kernel<<<grid_for(nnz), 256, 0, s>>>(stage, nnz, ctx->dims[m], idx32[m], ctx->errflag);
+            BL_CUDA(cudaGetLastError());
+        }
+    }
+    if (nnz > 0) {
+        BL_CUDA(cudaMemcpyAsync(vals, vals_in, nnz * 8, cudaMemcpyDefault, s));
+        check_values_kernel<<<grid_for(nnz), 256, 0, s>>>(vals, nnz, ctx->errflag);
+        BL_CUDA(cudaGetLastError());
+    }
+    int32_t hflag[4] = {0, 0, 0, 0};
+    BL_CUDA(cudaMemcpyAsync(hflag, ctx->errflag, 16, cudaMemcpyDeviceToHost, s));
+    BL_CUDA(cudaStreamSynchronize(s));
+    if (hflag[0]) {
+        cleanup();
+        return fail(ctx, CPAPR_E_RANGE, "a coordinate lies outside [0, I_m)");
+    }
+    if (hflag[1]) {
+        cleanup();
+        return fail(ctx, CPAPR_E_VALUE, "a tensor value is negative, NaN or infinite");
+    }
+    cudaFreeAsync(stage, s);
+    stage = nullptr;
+
+    BL_CUDA(cudaMallocAsync((void **)&keys, nb * 4, s));
+    BL_CUDA(cudaMallocAsync((void **)&perm, nb * 4, s));
+    BL_CUDA(cudaMallocAsync((void **)&tk, nb * 4, s));
+    BL_CUDA(cudaMallocAsync((void **)&tv, nb * 4, s));
+
+    for (int n = 0; n < N; ++n) {
+        ModeLayout &L = ctx->mode[n];
+        L.In = (int32_t)ctx->dims[n];
+        void *p = nullptr;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)(L.In + 1) * 4));
+        L.seg = (int32_t *)p;
+        int k = 0;
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
+            L.idx[k] = (int32_t *)p;
+            BL_CUDA(cudaMemsetAsync(p, 0, (size_t)np * 4, s));
+            ++k;
+        }
+        BL_TRY(dev_alloc(ctx, &p, (size_t)np * ctx->esize));
+        L.val = p;
+        BL_CUDA(cudaMemsetAsync(p, 0, (size_t)np * ctx->esize, s));
+        if (nnz == 0) {
+            BL_CUDA(cudaMemsetAsync(L.seg, 0, (size_t)(L.In + 1) * 4, s));
+            continue;
+        }
+        BL_CUDA(cudaMemcpyAsync(keys, idx32[n], nnz * 4, cudaMemcpyDeviceToDevice, s));
+        iota_kernel<<<grid_for(nnz), 256, 0, s>>>(perm, nnz);
+        BL_CUDA(cudaGetLastError());
+        int bits = 0;
+        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)L.In) ++bits;
+        BL_TRY(radix_sort(ctx, keys, perm, tk, tv, nnz, bits));
+        seg_kernel<<<grid_for(nnz), 256, 0, s>>>(keys, nnz, L.In, L.seg);
+        BL_CUDA(cudaGetLastError());
+        k = 0;
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            gather_i32_kernel<<<grid_for(nnz), 256, 0, s>>>(idx32[m], perm, nnz, L.idx[k]);
+            BL_CUDA(cudaGetLastError());
+            ++k;
+        }
+        if (ctx->esize == 8)
+            gather_val_kernel<double><<<grid_for(nnz), 256, 0, s>>>(vals, perm, nnz, (double *)L.val);
+        else
+            gather_val_kernel<float><<<grid_for(nnz), 256, 0, s>>>(vals, perm, nnz, (float *)L.val);
+        BL_CUDA(cudaGetLastError());
+    }
+    cleanup();
+    BL_CUDA(cudaStreamSynchronize(s));
+#undef BL_CUDA
+#undef BL_TRY
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tile tables
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t upper_bound_seg(const int32_t *seg, int32_t lo, int32_t hi, int64_t p) {
+    // first i in [lo, hi) with seg[i] > p (hi if none)
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)seg[mid] > p)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int32_t lower_bound_seg(const int32_t *seg, int32_t lo, int32_t hi, int64_t p) {
+    // first i in [lo, hi) with seg[i] >= p (hi if none)
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)seg[mid] >= p)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void tile_rows_kernel(const int32_t *__restrict__ seg, int32_t In, int64_t nnz, int32_t T, int32_t ntiles,
+                                 int32_t *__restrict__ row_first, int32_t *__restrict__ row_lo) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    int64_t p0 = (int64_t)t * T;
+    if (t < ntiles) {
+        row_first[t] = upper_bound_seg(seg, 0, In, p0) - 1;
+        row_lo[t] = lower_bound_seg(seg, 0, In, p0);
+    } else {
+        row_lo[t] = In;
+    }
+}
+
+__global__ void split_flags_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ row_first, int32_t T,
+                                   int32_t ntiles, uint32_t *__restrict__ flag) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    uint32_t f = 0;
+    if (t >= 1) {
+        int32_t r = row_first[t];
+        bool cut = (int64_t)seg[r] < (int64_t)t * T;
+        bool prev_cut = t >= 2 && row_first[t - 1] == r && (int64_t)seg[r] < (int64_t)(t - 1) * T;
+        f = (cut && !prev_cut) ? 1u : 0u;
+    }
+    flag[t] = f;
+}
+
+__global__ void split_write_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ row_first, int32_t T,
+                                   int32_t ntiles, const uint32_t *__restrict__ pos, int32_t *__restrict__ split) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 1 || t >= ntiles) return;
+    int32_t r = row_first[t];
+    bool cut = (int64_t)seg[r] < (int64_t)t * T;
+    bool prev_cut = t >= 2 && row_first[t - 1] == r && (int64_t)seg[r] < (int64_t)(t - 1) * T;
+    if (cut && !prev_cut) {
+        uint32_t k = pos[t];
+        split[3 * k + 0] = r;
+        split[3 * k + 1] = t - 1;
+        split[3 * k + 2] = (int32_t)(((int64_t)seg[r + 1] - 1) / T);
+    }
+}
+
+cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
+    ModeLayout &L = ctx->mode[n];
+    cudaStream_t s = ctx->stream;
+    if (L.row_first) cudaFreeAsync(L.row_first, s);
+    if (L.row_lo) cudaFreeAsync(L.row_lo, s);
+    if (L.split) cudaFreeAsync(L.split, s);
+    L.row_first = L.row_lo = L.split = nullptr;
+    L.tile_nnz = tile_nnz;
+    L.ntiles = (int32_t)ceil_div(ctx->nnz, tile_nnz);
+    L.nsplit = 0;
+    const int nt = L.ntiles;
+    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_first, (size_t)std::max(nt, 1) * 4, s));
+    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_lo, (size_t)(nt + 1) * 4, s));
+    tile_rows_kernel<<<(unsigned)ceil_div(nt + 1, 256), 256, 0, s>>>(L.seg, L.In, ctx->nnz, tile_nnz, nt, L.row_first,
+                                                                     L.row_lo);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    if (nt >= 2) {
+        uint32_t *flag = nullptr, *dtot = nullptr;
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&flag, (size_t)nt * 4 + 4, s));
+        dtot = flag + nt;
+        split_flags_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        CPAPR_TRY(exclusive_scan_u32(ctx, flag, nt, dtot));
+        uint32_t total = 0;
+        CPAPR_CUDA(ctx, cudaMemcpyAsync(&total, dtot, 4, cudaMemcpyDeviceToHost, s));
+        CPAPR_CUDA(ctx, cudaStreamSynchronize(s));
+        L.nsplit = (int32_t)total;
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, (size_t)std::max<int>(L.nsplit, 1) * 12, s));
+        split_write_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag, L.split);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        CPAPR_CUDA(ctx, cudaFreeAsync(flag, s));
+    } else {
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, 12, s));
+    }
+    // the carry buffer holds two partial rows per tile
+    int64_t need = (int64_t)2 * std::max(nt, 1) * ctx->Rp;
+    if (need > ctx->carry_elems) {
+        if (ctx->carry) cudaFreeAsync(ctx->carry, s);
+        ctx->carry = nullptr;
+        CPAPR_CUDA(ctx, cudaMallocAsync(&ctx->carry, (size_t)need * ctx->esize, s));
+        ctx->carry_elems = need;
+    }
+    int64_t llneed = std::max(nt, 1);
+    (void)llneed;
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(s));
+    return CPAPR_OK;
+}
+
+}  // namespace cpapr

@@ -1,0 +1,185 @@
+// Internal declarations of the CP-APR MU CUDA library (sm_103a).
+//
+// Device layout of one context (all allocations owned by the context):
+//   per mode n (sorted by i_n once, at create):
+//     seg[n]      int32 [I_n + 1]    first sorted position of each row
+//     idx[n][k]   int32 [nnz_pad]    coordinate of the k-th other mode (k = 0..N-2,
+//                                    increasing mode number), in mode-n order
+//     val[n]      T     [nnz_pad]    counts in mode-n order (T = double or float)
+//     tile table  row_first[t], row_lo[t] and the list of rows that span tiles
+//   model:  A[m] T [I_m x Rp], lambda double [Rp], B T [Imax x Rp],
+//           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration)
+//   scratch: carry T [2 x ntiles x Rp] (per-tile partial rows), reductions.
+// Rp is R rounded up so that one factor row is a whole number of 16-byte
+// vectors; the padding columns are zero everywhere and never leave the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cpapr.h"
+
+namespace cpapr {
+
+constexpr int kMaxModes = CPAPR_MAX_MODES;
+
+enum KernelKind { K_PHI = 0, K_FIXUP = 1, K_UPDATE = 2, K_NORM = 3, K_SB = 4, K_LL = 5, K_MTTKRP = 6, K_NKINDS = 7 };
+
+// Device-side state of one mode's inner loop (written by the kernels only).
+struct InnerState {
+    int32_t l;          // inner iteration about to run (0-based)
+    int32_t done;       // KKT check passed: skip the rest of the inner loop
+    int32_t used;       // inner iterations run
+    int32_t passed;     // 1 if the check passed (at iteration used)
+    uint32_t counter;   // last-block election counter
+    int32_t pad[3];
+    unsigned long long kkt[2];  // max violation of iteration l, as ordered bits of a double >= 0
+    double viol;        // last checked violation
+};
+
+struct ModeLayout {
+    int32_t In = 0;
+    int32_t *seg = nullptr;
+    int32_t *idx[kMaxModes - 1] = {};
+    void *val = nullptr;
+    // tiles
+    int32_t tile_nnz = 0, ntiles = 0, lanes = 1, reduction = CPAPR_REDUCE_SEGMENTED, threads = 256;
+    int32_t *row_first = nullptr;  // [ntiles]     row holding the tile's first nonzero
+    int32_t *row_lo = nullptr;     // [ntiles + 1] first row whose start lies in the tile; row_lo[ntiles] = In
+    int32_t nsplit = 0;
+    int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
+};
+
+struct cpapr_ctx_impl;
+
+}  // namespace cpapr
+
+struct cpapr_ctx {
+    int N = 0;
+    int64_t dims[CPAPR_MAX_MODES] = {};
+    int64_t nnz = 0;
+    int64_t nnz_pad = 0;
+    int R = 0, Rp = 0;
+    int Imax = 0;
+    cpapr_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    size_t esize = 8;  // bytes per element of the working precision
+    cpapr::ModeLayout mode[CPAPR_MAX_MODES];
+    // model
+    double *lambda = nullptr;
+    void *A[CPAPR_MAX_MODES] = {};
+    void *B = nullptr;
+    void *outbuf = nullptr;  // Phi / MTTKRP output of the one-off calls (Imax x Rp)
+    void *Phi[CPAPR_MAX_MODES] = {};
+    double *stage = nullptr;  // FP64 staging for I/O (Imax x Rp)
+    void *carry = nullptr;
+    int64_t carry_elems = 0;
+    double *colpart = nullptr;   // column-sum partials [kColParts x Rp]
+    double *colsum = nullptr;    // per-mode column sums [N x Rp]
+    double *llpart = nullptr;    // per-tile log-likelihood partials
+    cpapr::InnerState *inner = nullptr;  // [N]
+    double *scalars = nullptr;   // misc device scalars
+    int32_t *errflag = nullptr;  // device error flags
+    bool model_set = false;
+    int64_t k_total = 0;
+    bool sticky = false;
+    std::string err;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+    // profiling
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    int64_t prof_launches[cpapr::K_NKINDS] = {};
+    double prof_ms[cpapr::K_NKINDS] = {};
+    // graphs (one per mode and inner-loop bound)
+    cudaGraphExec_t graph_exec[CPAPR_MAX_MODES] = {};
+    int graph_max_inner[CPAPR_MAX_MODES] = {};
+    double graph_tol[CPAPR_MAX_MODES] = {};
+};
+
+namespace cpapr {
+
+constexpr int kColParts = 256;
+
+// ---- error plumbing ------------------------------------------------------
+cpapr_status fail(cpapr_ctx *ctx, cpapr_status st, const std::string &msg);
+cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what);
+
+#define CPAPR_CUDA(ctx, call)                                  \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return cpapr::cuda_fail((ctx), _e, #call); \
+    } while (0)
+
+#define CPAPR_TRY(expr)                       \
+    do {                                      \
+        cpapr_status _s = (expr);             \
+        if (_s != CPAPR_OK) return _s;        \
+    } while (0)
+
+cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes);
+
+// ---- profiling ------------------------------------------------------------
+struct ProfScope {
+    cpapr_ctx *ctx;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(cpapr_ctx *c, int k);
+    ~ProfScope();
+};
+void prof_collect(cpapr_ctx *ctx);
+
+// ---- index build (index.cu) ------------------------------------------------
+cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const double *vals_in);
+cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz);
+
+// ---- Phi family (phi.cu) -----------------------------------------------------
+enum PhiOp { OP_PHI = 0, OP_MTTKRP = 1, OP_LL = 2 };
+// Launches the tile kernel (+ fix-up) for mode n writing `out` (I_n x Rp).
+// B: I_n x Rp of the working type (ignored for MTTKRP).  inner: state whose
+// done flag / kkt slot the kernels use (may be null for a one-off Phi).
+cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner);
+// Sum of x log(m) over nonzeros, into llpart then *dst (device double).
+cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
+bool phi_config_supported(int esize, int nm1, int rp, int lanes);
+
+// ---- MU kernels (mu.cu) -------------------------------------------------------
+cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner);
+cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, InnerState *inner,
+                           unsigned long long cond_handle, int use_cond);
+cpapr_status launch_normalise(cpapr_ctx *ctx, int n);
+cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB);     // B = A^(n) diag(lambda)
+cpapr_status launch_colsums(cpapr_ctx *ctx);                          // colsum[m][r] for all m
+cpapr_status launch_ll_finish(cpapr_ctx *ctx, double *dst);           // dst -= sum_r lambda_r prod colsum
+cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed);
+cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst);   // R cols -> Rp cols, to T
+cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, double *dst); // Rp cols T -> R cols
+cpapr_status launch_kkt_rows(cpapr_ctx *ctx, int n, const void *B, const void *Phi, InnerState *inner);
+
+// ---- small utilities (index.cu) ---------------------------------------------
+cpapr_status exclusive_scan_u32(cpapr_ctx *ctx, uint32_t *data, int64_t n, uint32_t *total_out_dev);
+
+// ---- solver (solver.cu) -------------------------------------------------------
+cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, cpapr_result *res,
+                      int32_t *inner_trace, double *ll_trace);
+cpapr_status batch_mu_solve(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
+                            cpapr_result *results);
+
+// ---- device helpers -------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+    // v >= 0: IEEE bit patterns of non-negative doubles order like the values
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace cpapr

@@ -1,0 +1,382 @@
+// Kernels of the multiplicative-update loop around Phi (Algorithm 1 of
+// arXiv 2307.03276):
+//   B <- (A^(n) + S) Lambda            sb_kernel
+//   B <- B * Phi unless KKT passed     update_kernel (also the loop bookkeeping)
+//   lambda <- e^T B; A <- B Lambda^-1  colsum_partial_kernel + normalise_kernel
+// and the model I/O helpers.  All reductions that decide or normalise run in
+// FP64 whatever the working precision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace cpapr {
+
+static unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 152 * 8) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), cap));
+}
+
+// ---------------------------------------------------------------------------
+// B <- (A + S) Lambda.  S(i,r) = kappa when this is not the first outer
+// iteration, A(i,r) < kappa_tol and the previous Phi(i,r) > 1 (Chi and
+// Kolda's shift away from inadmissible zeros).  Also resets the mode's
+// inner-loop state.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void sb_kernel(const T *__restrict__ A, const T *__restrict__ phi_prev, const double *__restrict__ lambda,
+                          T *__restrict__ B, int64_t rows, int Rp, int shift, double kappa, double kappa_tol,
+                          InnerState *inner) {
+    if (inner && blockIdx.x == 0 && threadIdx.x == 0) {
+        inner->l = 0;
+        inner->done = 0;
+        inner->used = 0;
+        inner->passed = 0;
+        inner->counter = 0;
+        inner->kkt[0] = 0ull;
+        inner->kkt[1] = 0ull;
+        inner->viol = 0.0;
+    }
+    const int64_t n = rows * Rp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % Rp);
+        const double a = (double)A[e];
+        const double s = (shift && a < kappa_tol && (double)phi_prev[e] > 1.0) ? kappa : 0.0;
+        B[e] = (T)((a + s) * lambda[c]);
+    }
+}
+
+cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner) {
+    const int64_t rows = ctx->dims[n];
+    ProfScope ps(ctx, K_SB);
+    if (ctx->esize == 8)
+        sb_kernel<double><<<grid_for(rows * ctx->Rp), 256, 0, ctx->stream>>>(
+            (const double *)ctx->A[n], (const double *)ctx->Phi[n], ctx->lambda, (double *)ctx->B, rows, ctx->Rp,
+            shift ? 1 : 0, ctx->opt.kappa, ctx->opt.kappa_tol, inner);
+    else
+        sb_kernel<float><<<grid_for(rows * ctx->Rp), 256, 0, ctx->stream>>>(
+            (const float *)ctx->A[n], (const float *)ctx->Phi[n], ctx->lambda, (float *)ctx->B, rows, ctx->Rp,
+            shift ? 1 : 0, ctx->opt.kappa, ctx->opt.kappa_tol, inner);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// B <- B * Phi when the KKT check of this inner iteration failed.  Every
+// block reads the same published violation; the last block to finish does
+// the bookkeeping (iteration counter, done flag, next violation slot, and
+// the graph's loop condition).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void update_kernel(T *__restrict__ B, const T *__restrict__ P, int64_t n, InnerState *inner, double tol,
+                              int max_inner, cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ int s_l, s_done;
+    __shared__ double s_viol;
+    if (threadIdx.x == 0) {
+        s_l = *((volatile int32_t *)&inner->l);
+        s_done = *((volatile int32_t *)&inner->done);
+        s_viol = __longlong_as_double((long long)inner->kkt[s_l & 1]);
+    }
+    __syncthreads();
+    const int l = s_l, done = s_done;
+    const double viol = s_viol;
+    if (!done && !(viol < tol)) {
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+            B[e] = B[e] * P[e];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&inner->counter, 1u);
+        if (prev == gridDim.x - 1) {
+            inner->counter = 0;
+            int now_done = done;
+            if (!done) {
+                inner->viol = viol;
+                inner->used = l + 1;
+                if (viol < tol) {
+                    inner->done = 1;
+                    inner->passed = 1;
+                    now_done = 1;
+                }
+            }
+            inner->l = l + 1;
+            inner->kkt[(l + 1) & 1] = 0ull;
+            __threadfence();
+            if (use_cond) cudaGraphSetConditional(cond, (!now_done && l + 1 < max_inner) ? 1u : 0u);
+        }
+    }
+}
+
+cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, InnerState *inner,
+                           unsigned long long cond_handle, int use_cond) {
+    const int64_t nel = ctx->dims[n] * ctx->Rp;
+    ProfScope ps(ctx, K_UPDATE);
+    const unsigned g = grid_for(nel, 256, 152 * 4);
+    if (ctx->esize == 8)
+        update_kernel<double><<<g, 256, 0, ctx->stream>>>((double *)ctx->B, (const double *)ctx->Phi[n], nel, inner,
+                                                           tol, max_inner, (cudaGraphConditionalHandle)cond_handle,
+                                                           use_cond);
+    else
+        update_kernel<float><<<g, 256, 0, ctx->stream>>>((float *)ctx->B, (const float *)ctx->Phi[n], nel, inner, tol,
+                                                          max_inner, (cudaGraphConditionalHandle)cond_handle, use_cond);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// column sums (FP64), in a fixed order: block p sums rows p, p+P, ... per
+// column; the partials are then added in block order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void colsum_partial_kernel(const T *__restrict__ M, int64_t rows, int Rp, double *__restrict__ part) {
+    __shared__ double sm[256];
+    const int c = threadIdx.x % Rp;
+    const int rl = threadIdx.x / Rp;
+    const int nrl = blockDim.x / Rp;
+    double s = 0.0;
+    if (rl < nrl)
+        for (int64_t i = (int64_t)blockIdx.x * nrl + rl; i < rows; i += (int64_t)gridDim.x * nrl)
+            s += (double)M[i * Rp + c];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < Rp) {
+        double t = 0.0;
+        for (int k = 0; k < nrl; ++k) t += sm[k * Rp + threadIdx.x];
+        part[(int64_t)blockIdx.x * Rp + threadIdx.x] = t;
+    }
+}
+
+static int colsum_parts(int64_t rows, int Rp) {
+    const int nrl = std::max(1, 256 / Rp);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kColParts, ceil_div(rows, nrl * 4)));
+}
+
+// lambda_c = sum of partials; A(i,c) = B(i,c) / lambda_c, or A kept when
+// lambda_c = 0 (an all-zero column).
+template <typename T>
+__global__ void normalise_kernel(const T *__restrict__ B, T *__restrict__ A, int64_t rows, int Rp,
+                                 const double *__restrict__ part, int nparts, double *__restrict__ lambda) {
+    __shared__ double lam[256];
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * Rp + c];
+        lam[c] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < Rp; c += blockDim.x) lambda[c] = lam[c];
+    const int64_t n = rows * Rp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double l = lam[e % Rp];
+        if (l > 0.0) A[e] = (T)((double)B[e] / l);
+    }
+}
+
+cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
+    const int64_t rows = ctx->dims[n];
+    const int Rp = ctx->Rp;
+    const int parts = colsum_parts(rows, Rp);
+    ProfScope ps(ctx, K_NORM);
+    if (ctx->esize == 8) {
+        colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->B, rows, Rp, ctx->colpart);
+        normalise_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
+            (const double *)ctx->B, (double *)ctx->A[n], rows, Rp, ctx->colpart, parts, ctx->lambda);
+    } else {
+        colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->B, rows, Rp, ctx->colpart);
+        normalise_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
+            (const float *)ctx->B, (float *)ctx->A[n], rows, Rp, ctx->colpart, parts, ctx->lambda);
+    }
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// B = A^(n) diag(lambda)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void scale_b_kernel(const T *__restrict__ A, const double *__restrict__ lambda, T *__restrict__ B,
+                               int64_t n, int Rp) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        B[e] = (T)((double)A[e] * lambda[e % Rp]);
+}
+
+cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB) {
+    const int64_t nel = ctx->dims[n] * ctx->Rp;
+    if (ctx->esize == 8)
+        scale_b_kernel<double><<<grid_for(nel), 256, 0, ctx->stream>>>((const double *)ctx->A[n], ctx->lambda,
+                                                                       (double *)dstB, nel, ctx->Rp);
+    else
+        scale_b_kernel<float><<<grid_for(nel), 256, 0, ctx->stream>>>((const float *)ctx->A[n], ctx->lambda,
+                                                                      (float *)dstB, nel, ctx->Rp);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// column sums of every factor (for the log-likelihood's model total)
+// ---------------------------------------------------------------------------
+__global__ void reduce_parts_kernel(const double *__restrict__ part, int nparts, int Rp, double *__restrict__ dst) {
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * Rp + c];
+        dst[c] = s;
+    }
+}
+
+cpapr_status launch_colsums(cpapr_ctx *ctx) {
+    const int Rp = ctx->Rp;
+    for (int m = 0; m < ctx->N; ++m) {
+        const int64_t rows = ctx->dims[m];
+        const int parts = colsum_parts(rows, Rp);
+        if (ctx->esize == 8)
+            colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->A[m], rows, Rp,
+                                                                           ctx->colpart);
+        else
+            colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->A[m], rows, Rp,
+                                                                          ctx->colpart);
+        reduce_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->colpart, parts, Rp, ctx->colsum + (int64_t)m * Rp);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+    }
+    return CPAPR_OK;
+}
+
+// dst -= sum_r lambda_r prod_m colsum_m(r): the model's total over all entries
+__global__ void ll_finish_kernel(const double *__restrict__ lambda, const double *__restrict__ colsum, int N, int Rp,
+                                 double *__restrict__ dst) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tot = 0.0;
+    for (int c = 0; c < Rp; ++c) {
+        double p = lambda[c];
+        for (int m = 0; m < N; ++m) p *= colsum[(int64_t)m * Rp + c];
+        tot += p;
+    }
+    *dst = *dst - tot;
+}
+
+cpapr_status launch_ll_finish(cpapr_ctx *ctx, double *dst) {
+    CPAPR_TRY(launch_colsums(ctx));
+    ll_finish_kernel<<<1, 32, 0, ctx->stream>>>(ctx->lambda, ctx->colsum, ctx->N, ctx->Rp, dst);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// random initial model (SplitMix64, counter-based; Steele, Lea, Flood 2014)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void rand_fill_kernel(double *__restrict__ dst, int64_t rows, int R, int Rp, uint64_t base) {
+    const int64_t n = rows * Rp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / Rp;
+        const int c = (int)(e % Rp);
+        double v = 0.0;
+        if (c < R) {
+            const uint64_t k = (uint64_t)(i * R + c);
+            v = (double)(sm64_mix(base + (k + 1) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
+        }
+        dst[e] = v;
+    }
+}
+
+// A = stage / colsum (columns with a zero sum stay as they are); lambda *= colsum
+template <typename T>
+__global__ void init_scale_kernel(const double *__restrict__ stage, T *__restrict__ A, int64_t rows, int Rp,
+                                  const double *__restrict__ part, int nparts, double *__restrict__ lambda) {
+    __shared__ double cs[256];
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * Rp + c];
+        cs[c] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < Rp; c += blockDim.x) lambda[c] = lambda[c] * cs[c];
+    const int64_t n = rows * Rp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double s = cs[e % Rp];
+        A[e] = (T)(s > 0.0 ? stage[e] / s : stage[e]);
+    }
+}
+
+__global__ void fill_lambda_kernel(double *__restrict__ lambda, int R, int Rp) {
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) lambda[c] = c < R ? 1.0 : 0.0;
+}
+
+cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed) {
+    const int Rp = ctx->Rp;
+    fill_lambda_kernel<<<1, 256, 0, ctx->stream>>>(ctx->lambda, ctx->R, Rp);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    for (int m = 0; m < ctx->N; ++m) {
+        const int64_t rows = ctx->dims[m];
+        const uint64_t base = sm64_mix(seed + (uint64_t)(200 + m + 1) * 0x9E3779B97F4A7C15ull);
+        rand_fill_kernel<<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(ctx->stage, rows, ctx->R, Rp, base);
+        const int parts = colsum_parts(rows, Rp);
+        colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>(ctx->stage, rows, Rp, ctx->colpart);
+        if (ctx->esize == 8)
+            init_scale_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
+                ctx->stage, (double *)ctx->A[m], rows, Rp, ctx->colpart, parts, ctx->lambda);
+        else
+            init_scale_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
+                ctx->stage, (float *)ctx->A[m], rows, Rp, ctx->colpart, parts, ctx->lambda);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+    }
+    return CPAPR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// model I/O: caller matrices are rows x R doubles (host or device); the
+// device keeps rows x Rp of the working type with zero padding columns.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void convert_kernel(const double *__restrict__ src, T *__restrict__ dst, int64_t n,
+                               int32_t *__restrict__ errflag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[e];
+        if (!(v >= 0.0) || isinf(v)) atomicOr(errflag + 2, 1);
+        dst[e] = (T)v;
+    }
+}
+
+template <typename T>
+__global__ void widen_kernel(const T *__restrict__ src, double *__restrict__ dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
+cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst) {
+    const int R = ctx->R, Rp = ctx->Rp;
+    const int64_t n = rows * Rp;
+    CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->stage, 0, (size_t)n * 8, ctx->stream));
+    if (rows > 0)
+        CPAPR_CUDA(ctx, cudaMemcpy2DAsync(ctx->stage, (size_t)Rp * 8, src, (size_t)R * 8, (size_t)R * 8, (size_t)rows,
+                                          cudaMemcpyDefault, ctx->stream));
+    if (ctx->esize == 8)
+        convert_kernel<double><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (double *)dst, n, ctx->errflag);
+    else
+        convert_kernel<float><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (float *)dst, n, ctx->errflag);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, double *dst) {
+    const int R = ctx->R, Rp = ctx->Rp;
+    const int64_t n = rows * Rp;
+    const double *from = (const double *)src;
+    if (ctx->esize != 8) {
+        widen_kernel<float><<<grid_for(n), 256, 0, ctx->stream>>>((const float *)src, ctx->stage, n);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        from = ctx->stage;
+    }
+    if (rows > 0)
+        CPAPR_CUDA(ctx, cudaMemcpy2DAsync(dst, (size_t)R * 8, from, (size_t)Rp * 8, (size_t)R * 8, (size_t)rows,
+                                          cudaMemcpyDefault, ctx->stream));
+    return CPAPR_OK;
+}
+
+}  // namespace cpapr

@@ -1,0 +1,163 @@
+// Launchers for the Phi family (Phi^(n), MTTKRP, log-likelihood sum).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "phi_kernels.cuh"
+
+namespace cpapr {
+
+cudaError_t launch_phi_f64_n0(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f64_n2(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f64_n3(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f64_n4(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f32_n0(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f32_n2(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f32_n3(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f32_n4(const PhiArgs &, int, int, int, cudaStream_t);
+
+bool phi_config_supported(int esize, int nm1, int rp, int lanes) {
+    (void)nm1;
+    if (lanes < 1 || rp % lanes) return false;
+    const int rpl = rp / lanes;
+    if (esize == 8) {
+        static const int ok[][2] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {8, 2}, {16, 2}, {8, 4}, {16, 4}, {16, 8}};
+        for (auto &p : ok)
+            if (p[0] == rpl && p[1] == lanes) return true;
+    } else {
+        static const int ok[][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {4, 4},
+                                    {8, 4}, {4, 8}, {8, 8}, {4, 16}, {8, 16}};
+        for (auto &p : ok)
+            if (p[0] == rpl && p[1] == lanes) return true;
+    }
+    return false;
+}
+
+static cudaError_t dispatch(const cpapr_ctx *ctx, const PhiArgs &a, int rpl, int lanes, int op) {
+    const int nm1 = ctx->N - 1;
+    if (ctx->esize == 8) {
+        switch (nm1) {
+            case 2: return launch_phi_f64_n2(a, rpl, lanes, op, ctx->stream);
+            case 3: return launch_phi_f64_n3(a, rpl, lanes, op, ctx->stream);
+            case 4: return launch_phi_f64_n4(a, rpl, lanes, op, ctx->stream);
+            default: return launch_phi_f64_n0(a, rpl, lanes, op, ctx->stream);
+        }
+    }
+    switch (nm1) {
+        case 2: return launch_phi_f32_n2(a, rpl, lanes, op, ctx->stream);
+        case 3: return launch_phi_f32_n3(a, rpl, lanes, op, ctx->stream);
+        case 4: return launch_phi_f32_n4(a, rpl, lanes, op, ctx->stream);
+        default: return launch_phi_f32_n0(a, rpl, lanes, op, ctx->stream);
+    }
+}
+
+static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerState *inner) {
+    const ModeLayout &L = ctx->mode[n];
+    PhiArgs a{};
+    a.nnz = ctx->nnz;
+    a.T = L.tile_nnz;
+    a.ntiles = L.ntiles;
+    a.Rp = ctx->Rp;
+    a.In = L.In;
+    a.nm1 = ctx->N - 1;
+    a.atomic = L.reduction == CPAPR_REDUCE_ATOMIC ? 1 : 0;
+    a.seg = L.seg;
+    int k = 0;
+    for (int m = 0; m < ctx->N; ++m) {
+        if (m == n) continue;
+        a.idx[k] = L.idx[k];
+        a.A[k] = ctx->A[m];
+        ++k;
+    }
+    a.val = L.val;
+    a.B = B;
+    a.out = out;
+    a.carry = ctx->carry;
+    a.row_first = L.row_first;
+    a.row_lo = L.row_lo;
+    a.split = L.split;
+    a.nsplit = L.nsplit;
+    a.eps = ctx->opt.eps;
+    a.inner = inner;
+    a.llpart = ctx->llpart;
+    return a;
+}
+
+template <typename T>
+static cudaError_t run_fixup(const PhiArgs &a, int op, cudaStream_t s) {
+    if (a.nsplit <= 0) return cudaSuccess;
+    if (op == OP_PHI)
+        phi_fixup_kernel<T, OP_PHI><<<a.nsplit, 256, 0, s>>>(a);
+    else
+        phi_fixup_kernel<T, OP_MTTKRP><<<a.nsplit, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t run_kkt_rows(const T *B, const T *P, int64_t n, InnerState *inner, cudaStream_t s) {
+    int64_t g = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 8));
+    kkt_rows_kernel<T><<<(unsigned)g, 256, 0, s>>>(B, P, n, inner);
+    return cudaGetLastError();
+}
+
+cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner) {
+    ModeLayout &L = ctx->mode[n];
+    const int64_t nel = (int64_t)L.In * ctx->Rp;
+    PhiArgs a = make_args(ctx, n, B, out, inner);
+    const bool atomic = a.atomic && op != OP_LL;
+    if (ctx->nnz == 0 || atomic) {
+        CPAPR_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)nel * ctx->esize, ctx->stream));
+    }
+    if (ctx->nnz > 0) {
+        ProfScope ps(ctx, op == OP_MTTKRP ? K_MTTKRP : K_PHI);
+        cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, op);
+        if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "phi tile kernel");
+    }
+    if (ctx->nnz > 0 && !atomic && L.nsplit > 0) {
+        ProfScope ps(ctx, K_FIXUP);
+        cudaError_t e = ctx->esize == 8 ? run_fixup<double>(a, op, ctx->stream) : run_fixup<float>(a, op, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "phi fix-up kernel");
+    }
+    if (op == OP_PHI && inner && (atomic || ctx->nnz == 0)) {
+        cudaError_t e = ctx->esize == 8
+                            ? run_kkt_rows<double>((const double *)B, (const double *)out, nel, inner, ctx->stream)
+                            : run_kkt_rows<float>((const float *)B, (const float *)out, nel, inner, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kkt kernel");
+    }
+    return CPAPR_OK;
+}
+
+__global__ void sum_parts_kernel(const double *__restrict__ part, int n, double *__restrict__ dst) {
+    // one block, fixed order: per-thread strided sums, then a tree
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dst = sm[0];
+}
+
+cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst) {
+    const ModeLayout &L = ctx->mode[0];
+    if (ctx->nnz == 0) {
+        CPAPR_CUDA(ctx, cudaMemsetAsync(dst, 0, 8, ctx->stream));
+        return CPAPR_OK;
+    }
+    PhiArgs a = make_args(ctx, 0, B0, nullptr, nullptr);
+    a.atomic = 0;
+    {
+        ProfScope ps(ctx, K_LL);
+        cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_LL);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "log-likelihood kernel");
+        sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->llpart, L.ntiles, dst);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+    }
+    return CPAPR_OK;
+}
+
+}  // namespace cpapr

@@ -1,0 +1,6 @@
+// Phi / MTTKRP / log-likelihood tile kernels: float, 4-way tensors.
+#define PHI_T float
+#define PHI_IS_DOUBLE 0
+#define PHI_NM1 3
+#define PHI_FN launch_phi_f32_n3
+#include "phi_inst.cuh"

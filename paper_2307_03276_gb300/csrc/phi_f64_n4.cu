@@ -1,0 +1,6 @@
+// Phi / MTTKRP / log-likelihood tile kernels: double, 5-way tensors.
+#define PHI_T double
+#define PHI_IS_DOUBLE 1
+#define PHI_NM1 4
+#define PHI_FN launch_phi_f64_n4
+#include "phi_inst.cuh"

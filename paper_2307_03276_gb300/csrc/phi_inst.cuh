@@ -1,0 +1,72 @@
+// Instantiates the Phi tile kernels for one working type (PHI_T) and one
+// gathered-mode count (PHI_NM1; 0 = runtime count) and exposes a launcher.
+// Included by the small phi_<type>_<nm1>.cu units so that the template
+// instantiations compile in parallel.
+#include "phi_kernels.cuh"
+
+#ifndef PHI_T
+#error "define PHI_T"
+#endif
+#ifndef PHI_NM1
+#error "define PHI_NM1"
+#endif
+#ifndef PHI_FN
+#error "define PHI_FN"
+#endif
+
+namespace cpapr {
+
+namespace {
+constexpr int kThreads = sizeof(PHI_T) == 8 ? 128 : 256;
+constexpr int kUnroll = sizeof(PHI_T) == 8 ? 1 : 2;
+
+template <int RPL, int G, int OP>
+cudaError_t run(const PhiArgs &a, cudaStream_t s) {
+    auto k = phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, kUnroll>;
+    size_t smem = 0;
+    if (OP != OP_LL && !a.atomic) smem = (size_t)2 * kThreads * RPL * sizeof(PHI_T) + (size_t)2 * (kThreads / G) * 4;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.ntiles > 0) k<<<a.ntiles, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// Returns cudaErrorInvalidValue when (rpl, lanes) has no instantiation.
+cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s) {
+#define CPAPR_CASE(R_, G_)                                                   \
+    if (rpl == R_ && lanes == G_) {                                          \
+        if (op == OP_PHI) return run<R_, G_, OP_PHI>(a, s);                  \
+        if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP>(a, s);            \
+        return run<R_, G_, OP_LL>(a, s);                                     \
+    }
+#if PHI_IS_DOUBLE
+    CPAPR_CASE(2, 1)
+    CPAPR_CASE(4, 1)
+    CPAPR_CASE(8, 1)
+    CPAPR_CASE(16, 1)
+    CPAPR_CASE(8, 2)
+    CPAPR_CASE(16, 2)
+    CPAPR_CASE(8, 4)
+    CPAPR_CASE(16, 4)
+    CPAPR_CASE(16, 8)
+#else
+    CPAPR_CASE(4, 1)
+    CPAPR_CASE(8, 1)
+    CPAPR_CASE(16, 1)
+    CPAPR_CASE(4, 2)
+    CPAPR_CASE(8, 2)
+    CPAPR_CASE(4, 4)
+    CPAPR_CASE(8, 4)
+    CPAPR_CASE(4, 8)
+    CPAPR_CASE(8, 8)
+    CPAPR_CASE(4, 16)
+    CPAPR_CASE(8, 16)
+#endif
+#undef CPAPR_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cpapr

@@ -1,0 +1,461 @@
+// Phi^(n) tile kernels (Algorithm 2 of arXiv 2307.03276, evaluated per
+// nonzero as in Algorithm 3) and their two variants that share the same
+// gather: MTTKRP (Experiment 8: no dot product, no division) and the
+// log-likelihood sum (the dot product alone).
+//
+// Work decomposition.  Nonzeros of mode n are sorted by i_n.  A thread block
+// takes one tile of `tile_nnz` consecutive sorted nonzeros.  Inside the tile
+// a "group" of G lanes owns a contiguous run of nonzeros and walks it in
+// order; each lane holds RPL consecutive ranks of every row it touches, so
+// the G lanes of a group read a factor row (Rp = G * RPL entries) as one
+// coalesced 16-byte-vector access, and the dot product <B[i_n], pi> is summed
+// across the group with xor shuffles.  While consecutive nonzeros share a
+// row the group adds v * pi into registers; when the row changes it flushes.
+//
+// Same-row reduction without atomics (the paper's atomic-mitigation idea of
+// Algorithm 4 taken to three levels):
+//   1. a row that starts and ends inside a group's run is stored directly;
+//   2. a row cut by group boundaries leaves a head or tail partial in shared
+//      memory; after a barrier the block adds each chain of partials in group
+//      order and stores the row if it ends inside the tile;
+//   3. a row cut by a tile boundary leaves a per-tile partial in the carry
+//      buffer; the fix-up kernel adds the partials of every such row in tile
+//      order (a fixed order, so results are bit-reproducible).
+// Rows whose first position lies in the tile but hold no nonzero are
+// written as zeros by that tile.  With reduction = ATOMIC, levels 2 and 3 are
+// replaced by atomic adds into a zeroed output.
+//
+// The KKT violation max_{i,r} |min(B, 1 - Phi)| of the MU loop is folded in:
+// whoever writes a final Phi row also reduces its violation, and one atomicMax
+// per block publishes it (non-negative doubles order like their bit patterns).
+//
+// FP32 form: gathers, Khatri-Rao products, dot and scale in FP32; every
+// row sum (run accumulation, chain and carry sums) is Kahan-compensated;
+// the violation and the log-likelihood are reduced in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cpapr {
+
+constexpr int kMaxNm1 = kMaxModes - 1;
+
+struct PhiArgs {
+    int64_t nnz;
+    int32_t T;       // nonzeros per tile
+    int32_t ntiles;
+    int32_t Rp;
+    int32_t In;
+    int32_t nm1;     // number of gathered modes (N - 1)
+    int32_t atomic;  // 1: partial rows are added with atomics into a zeroed output
+    const int32_t *seg;
+    const int32_t *idx[kMaxNm1];
+    const void *val;
+    const void *A[kMaxNm1];
+    const void *B;
+    void *out;
+    void *carry;     // head partials [ntiles][Rp], then tail partials [ntiles][Rp]
+    const int32_t *row_first;
+    const int32_t *row_lo;
+    const int32_t *split;
+    int32_t nsplit;
+    double eps;
+    InnerState *inner;  // null for a one-off Phi (no KKT bookkeeping)
+    double *llpart;     // OP_LL: one partial per tile
+};
+
+// ---- compensated sums --------------------------------------------------------
+template <typename T> struct KSum {
+    T s, c;
+    __device__ __forceinline__ void zero() { s = T(0); c = T(0); }
+    __device__ __forceinline__ void add(T x) { s += x; }
+    __device__ __forceinline__ void fma_add(T v, T p) { s = fma(v, p, s); }
+    __device__ __forceinline__ T value() const { return s; }
+};
+template <> struct KSum<float> {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    // Kahan (1965): carry the rounding error of every addition in c
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ void fma_add(float v, float p) { add(v * p); }
+    __device__ __forceinline__ float value() const { return s - c; }
+};
+
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+template <typename T> __device__ __forceinline__ double row_violation(T b, T phi) {
+    double bb = (double)b, pp = (double)phi;
+    double m = bb < 1.0 - pp ? bb : 1.0 - pp;
+    return fabs(m);
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduces the block's violation and publishes it into inner->kkt[l & 1].
+template <int THREADS>
+__device__ __forceinline__ void publish_kkt(double v, InnerState *inner, double *sm) {
+    v = warp_max(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; ++w) m = fmax(m, sm[w]);
+        if (m > 0.0) atomicMax(&inner->kkt[inner->l & 1], ordered_bits(m));
+    }
+}
+
+__device__ __forceinline__ int32_t ub_seg(const int32_t *__restrict__ seg, int32_t lo, int32_t hi, int64_t p) {
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)__ldg(seg + mid) > p)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+template <typename T, int RPL>
+__device__ __forceinline__ void load_row(const T *__restrict__ base, T (&dst)[RPL]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    const V *p = reinterpret_cast<const V *>(base);
+#pragma unroll
+    for (int v = 0; v < RPL / VN; ++v) {
+        V x = __ldg(p + v);
+        if constexpr (VN == 4) {
+            dst[4 * v + 0] = x.x;
+            dst[4 * v + 1] = x.y;
+            dst[4 * v + 2] = x.z;
+            dst[4 * v + 3] = x.w;
+        } else {
+            dst[2 * v + 0] = x.x;
+            dst[2 * v + 1] = x.y;
+        }
+    }
+}
+
+template <typename T, int RPL>
+__device__ __forceinline__ void mul_row(const T *__restrict__ base, T (&dst)[RPL]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    const V *p = reinterpret_cast<const V *>(base);
+#pragma unroll
+    for (int v = 0; v < RPL / VN; ++v) {
+        V x = __ldg(p + v);
+        if constexpr (VN == 4) {
+            dst[4 * v + 0] *= x.x;
+            dst[4 * v + 1] *= x.y;
+            dst[4 * v + 2] *= x.z;
+            dst[4 * v + 3] *= x.w;
+        } else {
+            dst[2 * v + 0] *= x.x;
+            dst[2 * v + 1] *= x.y;
+        }
+    }
+}
+
+template <typename T, int RPL>
+__device__ __forceinline__ void store_row(T *__restrict__ base, const T (&src)[RPL]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    V *p = reinterpret_cast<V *>(base);
+#pragma unroll
+    for (int v = 0; v < RPL / VN; ++v) {
+        V x;
+        if constexpr (VN == 4) {
+            x.x = src[4 * v + 0];
+            x.y = src[4 * v + 1];
+            x.z = src[4 * v + 2];
+            x.w = src[4 * v + 3];
+        } else {
+            x.x = src[2 * v + 0];
+            x.y = src[2 * v + 1];
+        }
+        p[v] = x;
+    }
+}
+
+// NM1: number of gathered modes (exact), or 0 for "runtime count up to kMaxNm1".
+// U: nonzeros whose gathers are issued together (memory-level parallelism).
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+__global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
+    constexpr int NG = THREADS / G;
+    constexpr int NWARPS = THREADS / 32;
+    constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
+    if (a.inner && a.inner->done) return;
+    const int nm1 = NM1 > 0 ? NM1 : a.nm1;
+    const int tid = threadIdx.x;
+    const int g = tid / G, lane = tid % G;
+    const int warp = tid >> 5, wlane = tid & 31;
+    const int t = blockIdx.x;
+    const int Rp = RPL * G;
+    const int64_t p0 = (int64_t)t * a.T;
+    const int64_t p1 = min(p0 + (int64_t)a.T, a.nnz);
+    const int64_t vlen = ((int64_t)a.T + NG - 1) / NG;
+    const int64_t ga = min(p0 + (int64_t)g * vlen, p1);
+    const int64_t gb = min(ga + vlen, p1);
+    const int col0 = lane * RPL;
+    const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((wlane / G) * G));
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *slot_val = reinterpret_cast<T *>(smem_raw);                  // [2 * NG][Rp]
+    int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
+    __shared__ double red[NWARPS];
+
+    const bool segmented = (OP != OP_LL) && !a.atomic;
+    if (segmented) {
+        for (int s = tid; s < 2 * NG; s += THREADS) slot_row[s] = -1;
+        __syncthreads();
+    }
+
+    const int32_t *__restrict__ seg = a.seg;
+    const T *__restrict__ val = reinterpret_cast<const T *>(a.val);
+    const T *__restrict__ Bm = reinterpret_cast<const T *>(a.B);
+    T *__restrict__ out = reinterpret_cast<T *>(a.out);
+    const T eps = (T)a.eps;
+
+    double kkt = 0.0;
+    double ll = 0.0;
+
+    if (ga < gb) {
+        int32_t row = ub_seg(seg, a.row_first[t], a.row_lo[t + 1], ga) - 1;
+        int64_t rend = __ldg(seg + row + 1);
+        int64_t rbeg = __ldg(seg + row);
+        int32_t cur = row;
+        int64_t cbeg = rbeg, cend = rend;
+        KSum<T> acc[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) acc[r].zero();
+        T brow[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) brow[r] = T(0);
+
+        auto flush = [&](int32_t frow, int64_t fbeg, int64_t fend) {
+            T v[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) v[r] = acc[r].value();
+            if (fbeg >= ga && fend <= gb) {
+                store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
+                if (OP == OP_PHI) {
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) kkt = fmax(kkt, row_violation(brow[r], v[r]));
+                }
+            } else if (a.atomic) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) atomicAdd(out + (int64_t)frow * Rp + col0 + r, v[r]);
+            } else {
+                const int s = fbeg < ga ? 2 * g : 2 * g + 1;
+                if (lane == 0) slot_row[s] = frow;
+                store_row<T, RPL>(slot_val + (int64_t)s * Rp + col0, v);
+            }
+        };
+
+        for (int64_t q = ga; q < gb; q += U) {
+            int32_t ii[U][MAXK];
+            T xx[U];
+            int32_t rr[U];
+            int64_t rb[U], re[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t qq = min(q + u, gb - 1);
+                xx[u] = __ldg(val + qq);
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k)
+                    if (k < nm1) ii[u][k] = __ldg(a.idx[k] + qq);
+                while (qq >= rend) {
+                    ++row;
+                    rbeg = rend;
+                    rend = __ldg(seg + row + 1);
+                }
+                rr[u] = row;
+                rb[u] = rbeg;
+                re[u] = rend;
+            }
+            T pi[U][RPL];
+            T bb[U][RPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_row<T, RPL>(reinterpret_cast<const T *>(a.A[0]) + (int64_t)ii[u][0] * Rp + col0, pi[u]);
+#pragma unroll
+                for (int k = 1; k < MAXK; ++k)
+                    if (k < nm1) mul_row<T, RPL>(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[u][k] * Rp + col0, pi[u]);
+                if (OP != OP_MTTKRP) load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, bb[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q + u < gb) {
+                    if (OP != OP_LL && rr[u] != cur) {
+                        flush(cur, cbeg, cend);
+                        cur = rr[u];
+                        cbeg = rb[u];
+                        cend = re[u];
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) acc[r].zero();
+                    }
+                    if (OP == OP_MTTKRP) {
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) acc[r].fma_add(xx[u], pi[u][r]);
+                    } else {
+                        T s = T(0);
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) s = fma(bb[u][r], pi[u][r], s);
+#pragma unroll
+                        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+                        if (OP == OP_PHI) {
+                            const T v = xx[u] / tmax(s, eps);
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r) {
+                                acc[r].fma_add(v, pi[u][r]);
+                                brow[r] = bb[u][r];
+                            }
+                        } else {  // OP_LL: x log(m) with m = <lambda o A^(n)[i_n], pi>
+                            if (lane == 0) {
+                                if constexpr (sizeof(T) == 8)
+                                    ll += (double)xx[u] * log((double)s);
+                                else
+                                    ll += (double)xx[u] * (double)logf((float)s);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (OP != OP_LL) flush(cur, cbeg, cend);
+    }
+
+    if (OP == OP_LL) {
+        double v = warp_sum(ll);
+        if (wlane == 0) red[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWARPS; ++w) s += red[w];
+            a.llpart[t] = s;
+        }
+        return;
+    }
+
+    if (segmented) {
+        __syncthreads();
+        // chains of partials: slot 0 (a row that began before the tile) and
+        // every tail slot start a chain that continues through the head slots
+        // of the following groups while they hold the same row
+        T *carry_head = reinterpret_cast<T *>(a.carry) + (int64_t)t * Rp;
+        T *carry_tail = reinterpret_cast<T *>(a.carry) + ((int64_t)a.ntiles + t) * Rp;
+        for (int s = warp; s < 2 * NG; s += NWARPS) {
+            if (!(s == 0 || (s & 1))) continue;
+            const int32_t crow = slot_row[s];
+            if (crow < 0) continue;
+            const int gs = s >> 1;
+            int gend = gs + 1;
+            while (gend < NG && slot_row[2 * gend] == crow) ++gend;
+            const bool complete = s != 0 && (int64_t)__ldg(seg + crow + 1) <= p1;
+            for (int c = wlane; c < Rp; c += 32) {
+                KSum<T> sum;
+                sum.zero();
+                sum.add(slot_val[(int64_t)s * Rp + c]);
+                for (int k = gs + 1; k < gend; ++k) sum.add(slot_val[(int64_t)(2 * k) * Rp + c]);
+                const T v = sum.value();
+                if (s == 0) {
+                    carry_head[c] = v;
+                } else if (complete) {
+                    out[(int64_t)crow * Rp + c] = v;
+                    if (OP == OP_PHI) kkt = fmax(kkt, row_violation(__ldg(Bm + (int64_t)crow * Rp + c), v));
+                } else {
+                    carry_tail[c] = v;
+                }
+            }
+        }
+        // rows owned by this tile that hold no nonzero: Phi row = 0
+        const int32_t rlo = a.row_lo[t], rhi = a.row_lo[t + 1];
+        for (int32_t i = rlo + warp; i < rhi; i += NWARPS) {
+            if (__ldg(seg + i) == __ldg(seg + i + 1)) {
+                for (int c = wlane; c < Rp; c += 32) {
+                    out[(int64_t)i * Rp + c] = T(0);
+                    if (OP == OP_PHI) kkt = fmax(kkt, row_violation(__ldg(Bm + (int64_t)i * Rp + c), T(0)));
+                }
+            }
+        }
+    }
+    if (OP == OP_PHI && a.inner && !a.atomic) publish_kkt<THREADS>(kkt, a.inner, red);
+}
+
+// Adds the per-tile partials of every row that spans tiles, in tile order,
+// and stores the row (plus its KKT violation).  One block per such row.
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
+    if (a.inner && a.inner->done) return;
+    __shared__ T sm_s[256];
+    __shared__ T sm_c[256];
+    __shared__ double red[8];
+    const int Rp = a.Rp;
+    const int32_t row = a.split[3 * blockIdx.x + 0];
+    const int32_t t0 = a.split[3 * blockIdx.x + 1];
+    const int32_t t1 = a.split[3 * blockIdx.x + 2];
+    const int c = threadIdx.x % Rp;
+    const int chunk = threadIdx.x / Rp;
+    const int nchunks = blockDim.x / Rp;
+    const T *carry = reinterpret_cast<const T *>(a.carry);
+    const int npart = t1 - t0 + 1;
+    KSum<T> sum;
+    sum.zero();
+    if (chunk < nchunks) {
+        for (int k = chunk; k < npart; k += nchunks) {
+            const int64_t off = k == 0 ? ((int64_t)a.ntiles + t0) * Rp : (int64_t)(t0 + k) * Rp;
+            sum.add(carry[off + c]);
+        }
+    }
+    sm_s[threadIdx.x] = sum.s;
+    sm_c[threadIdx.x] = sum.c;
+    __syncthreads();
+    double kkt = 0.0;
+    if (threadIdx.x < Rp) {
+        KSum<T> tot;
+        tot.zero();
+        for (int k = 0; k < nchunks; ++k) {
+            tot.add(sm_s[k * Rp + c]);
+            tot.add(-sm_c[k * Rp + c]);
+        }
+        const T v = tot.value();
+        reinterpret_cast<T *>(a.out)[(int64_t)row * Rp + c] = v;
+        if (OP == OP_PHI)
+            kkt = row_violation(reinterpret_cast<const T *>(a.B)[(int64_t)row * Rp + c], v);
+    }
+    if (OP == OP_PHI && a.inner) publish_kkt<256>(kkt, a.inner, red);
+}
+
+// KKT violation over all rows (used after the atomic reduction).
+template <typename T>
+__global__ void __launch_bounds__(256) kkt_rows_kernel(const T *__restrict__ B, const T *__restrict__ P, int64_t n,
+                                                        InnerState *inner) {
+    if (inner->done) return;
+    __shared__ double red[8];
+    double v = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        v = fmax(v, row_violation(B[e], P[e]));
+    publish_kkt<256>(v, inner, red);
+}
+
+}  // namespace cpapr

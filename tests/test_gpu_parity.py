@@ -1,0 +1,362 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (per entry, relative):
+  FP64 Phi / MTTKRP 1e-12 -- all terms are non-negative, so only summation
+      order differs; a segmented sum of k terms errs by about log2(k) ulps.
+  FP32 Phi / MTTKRP 1e-5 -- each term carries about (N - 1 + R + 4) FP32
+      roundings (factor conversion, Khatri-Rao product, dot, divide) and the
+      row sums are Kahan-compensated.
+  log-likelihood: FP64 1e-11 relative (a sum with cancellation against the
+      model total), FP32 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_03276_gb300 import cpapr, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2307_03276_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def max_rel(got, want):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    nz = want != 0
+    err = np.zeros_like(want)
+    err[nz] = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+    err[~nz] = np.abs(got[~nz]) > 0
+    return float(err.max()) if err.size else 0.0
+
+
+def make_case(name):
+    if name == "c1":
+        return synth.generate(synth.C1)
+    if name == "c2s":
+        return synth.generate(synth.scaled(synth.C2, 200_000, dims=(20_000, 20_000, 1_000)))
+    if name == "c3s":
+        return synth.generate(synth.scaled(synth.C3, 300_000, dims=(40_000, 40_000, 10_000, 365)))
+    if name == "c5s":
+        return synth.generate(synth.scaled(synth.C5, 200_000, dims=(5_000, 5_000, 500, 100, 24), rank=8))
+    if name == "c5s64":
+        return synth.generate(synth.scaled(synth.C5, 100_000, dims=(5_000, 5_000, 500, 100, 24), rank=64))
+    if name == "n2":
+        return synth.random_tensor((300, 200), 5_000, 4, 77)
+    if name == "n6":
+        return synth.random_tensor((10, 9, 8, 7, 6, 5), 3_000, 8, 78)
+    raise KeyError(name)
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        _cache[name] = make_case(name)
+    return _cache[name]
+
+
+def model_for(T, seed=5):
+    fs = synth.random_factors(T.dims, T.rank, seed)
+    lam = 0.5 + synth.uniform01(synth.stream_base(seed, 999), 0, T.rank)
+    return lam, fs
+
+
+CASES = ["c1", "c2s", "c3s", "c5s", "c5s64", "n2", "n6"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("reduction", [cpapr.CPAPR_REDUCE_SEGMENTED, cpapr.CPAPR_REDUCE_ATOMIC])
+def test_phi_fp64_matches_oracle(name, reduction):
+    T = case(name)
+    lam, fs = model_for(T)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, reduction=reduction) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            got = t.phi(n)
+            assert max_rel(got, want) <= 1e-12, (name, n)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s64"])
+@pytest.mark.parametrize("tile", [64, 320, 8192])
+def test_phi_fp64_tile_sizes(name, tile):
+    """Small tiles cut many rows across tiles and groups (fix-up path), large ones few."""
+    T = case(name)
+    lam, fs = model_for(T, 9)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=tile) as t:
+        t.set_model(lam, fs)
+        info = t.info()
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= 1e-12, (name, tile, n, info.nsplit[n])
+
+
+@pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s", "c5s64", "n6"])
+def test_phi_fp32_matches_oracle(name):
+    T = case(name)
+    lam, fs = model_for(T)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=cpapr.CPAPR_FP32) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= 1e-5, (name, n)
+
+
+@pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_phi_rank_lanes(precision, tol, lanes):
+    """Every supported lanes-per-nonzero choice gives the same Phi."""
+    T = case("c3s")
+    lam, fs = model_for(T, 11)
+    from paper_2307_03276_gb300.cpapr import CpaprError
+    try:
+        t = cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, rank_lanes=lanes, tile_nnz=1024)
+    except CpaprError:
+        pytest.skip("lanes choice not instantiated for this rank/precision")
+    with t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= tol, (lanes, n)
+
+
+@pytest.mark.parametrize("name", ["c1", "c3s", "c5s", "n6"])
+@pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)])
+def test_mttkrp_matches_oracle(name, precision, tol):
+    T = case(name)
+    lam, fs = model_for(T)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            assert max_rel(t.mttkrp(n), oracle.mttkrp(T.dims, T.idx, T.vals, fs, n)) <= tol, (name, n)
+
+
+@pytest.mark.parametrize("name", ["c1", "c3s", "c5s"])
+@pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-11), (cpapr.CPAPR_FP32, 1e-5)])
+def test_loglik_matches_oracle(name, precision, tol):
+    T = case(name)
+    lam, fs = model_for(T)
+    want = oracle.loglik(T.dims, T.idx, T.vals, lam, fs)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) as t:
+        t.set_model(lam, fs)
+        got = t.loglik()
+    assert abs(got - want) <= tol * abs(want), (got, want)
+
+
+def test_explicit_b_with_epsilon_clamp():
+    """A zero row of B clamps every denominator of that slice to eps (Algorithm 2)."""
+    T = case("c1")
+    lam, fs = model_for(T)
+    B = fs[0] * 2.0
+    B[3] = 0.0
+    B[7, :] = 1e-30
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.set_model(lam, fs)
+        got = t.phi(0, B=B)
+    want = oracle.phi(T.dims, T.idx, T.vals, fs, B, 0)
+    assert max_rel(got, want) <= 1e-12
+
+
+def test_phi_deterministic_segmented():
+    T = case("c2s")
+    lam, fs = model_for(T)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=256) as t:
+        t.set_model(lam, fs)
+        a = t.phi(0)
+        b = t.phi(0)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_mu_solve_fp64_matches_oracle_c1(use_graph):
+    """Ten outer iterations of Algorithm 1 on the 100x80x60 tensor."""
+    T = case("c1")
+    lam, fs = model_for(T, 21)
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=10, max_inner=10)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, use_graph=use_graph) as t:
+        t.set_model(lam, fs)
+        res = t.mu_solve(tol=1e-4, max_outer=10, max_inner=10, trace=True)
+        lam_g, fs_g = t.get_model()
+    assert res["outer_iters"] == ref["outer_iters"]
+    assert np.array_equal(res["inner"], ref["inner"])
+    assert res["total_inner"] == ref["total_inner"]
+    assert max_rel(lam_g, ref["lambda"]) <= 1e-10
+    for A, Ar in zip(fs_g, ref["factors"]):
+        np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
+    np.testing.assert_allclose(res["loglik_trace"], ref["loglik"], rtol=1e-11)
+    assert abs(res["loglik"] - ref["loglik"][-1]) <= 1e-11 * abs(ref["loglik"][-1])
+
+
+def test_mu_solve_fp64_4way_two_outer():
+    T = case("c3s")
+    lam, fs = model_for(T, 22)
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=2, max_inner=4)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.set_model(lam, fs)
+        res = t.mu_solve(tol=1e-4, max_outer=2, max_inner=4, trace=True)
+        lam_g, fs_g = t.get_model()
+    assert np.array_equal(res["inner"], ref["inner"])
+    assert max_rel(lam_g, ref["lambda"]) <= 1e-10
+    for A, Ar in zip(fs_g, ref["factors"]):
+        np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
+
+
+def test_mu_solve_fp32_close_to_oracle():
+    T = case("c1")
+    lam, fs = model_for(T, 23)
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=3, max_inner=5)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=cpapr.CPAPR_FP32) as t:
+        t.set_model(lam, fs)
+        res = t.mu_solve(tol=1e-4, max_outer=3, max_inner=5)
+        lam_g, fs_g = t.get_model()
+    assert max_rel(lam_g, ref["lambda"]) <= 1e-4
+    assert abs(res["loglik"] - ref["loglik"][-1]) <= 1e-5 * abs(ref["loglik"][-1])
+
+
+def test_solve_resumes_across_calls():
+    """Two calls of one outer iteration equal one call of two (S from the 2nd on), bit for bit."""
+    T = case("c1")
+    lam, fs = model_for(T, 24)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.set_model(lam, fs)
+        t.mu_solve(tol=1e-4, max_outer=1, max_inner=5)
+        t.mu_solve(tol=1e-4, max_outer=1, max_inner=5)
+        a = t.get_model()
+        t.set_model(lam, fs)
+        t.mu_solve(tol=1e-4, max_outer=2, max_inner=5)
+        b = t.get_model()
+    assert np.array_equal(a[0], b[0])
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+
+
+def test_init_random_matches_oracle():
+    T = case("c1")
+    lo, fo = oracle.init_random(T.dims, T.rank, 4242)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.init_random(4242)
+        lg, fg = t.get_model()
+    assert max_rel(lg, lo) <= 1e-13
+    for a, b in zip(fg, fo):
+        assert max_rel(a, b) <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_tensor():
+    dims = (5, 4, 3)
+    idx = np.zeros((3, 0), dtype=np.int64)
+    vals = np.zeros(0)
+    fs = synth.random_factors(dims, 2, 1)
+    lam = np.ones(2)
+    with cpapr.Tensor(dims, idx, vals, 2) as t:
+        t.set_model(lam, fs)
+        for n in range(3):
+            assert np.all(t.phi(n) == 0.0)
+            assert np.all(t.mttkrp(n) == 0.0)
+        ll = t.loglik()
+    assert abs(ll - oracle.loglik(dims, idx, vals, lam, fs)) <= 1e-12 * abs(ll)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 7, 5), (9, 1, 4, 1)])
+def test_single_nonzero_and_unit_modes(dims):
+    idx = np.array([[d - 1] for d in dims], dtype=np.int64)
+    vals = np.array([3.0])
+    fs = synth.random_factors(dims, 3, 2)
+    lam = np.ones(3)
+    with cpapr.Tensor(dims, idx, vals, 3) as t:
+        t.set_model(lam, fs)
+        for n in range(len(dims)):
+            want = oracle.phi(dims, idx, vals, fs, fs[n], n)
+            assert max_rel(t.phi(n), want) <= 1e-12
+
+
+def test_heavy_row_spanning_many_tiles():
+    """One row holds 60% of the nonzeros and spans hundreds of tiles."""
+    rng = np.random.default_rng(3)
+    nnz = 200_000
+    dims = (50, 3000, 2000)
+    i0 = np.where(rng.random(nnz) < 0.6, 17, rng.integers(0, 50, nnz))
+    idx = np.stack([i0, rng.integers(0, 3000, nnz), rng.integers(0, 2000, nnz)]).astype(np.int64)
+    vals = rng.integers(1, 5, nnz).astype(np.float64)
+    fs = synth.random_factors(dims, 16, 4)
+    lam = np.ones(16)
+    for prec, tol in [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)]:
+        with cpapr.Tensor(dims, idx, vals, 16, tile_nnz=512, precision=prec) as t:
+            t.set_model(lam, fs)
+            want = oracle.phi(dims, idx, vals, fs, fs[0], 0)
+            assert max_rel(t.phi(0), want) <= tol
+
+
+def test_empty_slices_and_duplicates():
+    rng = np.random.default_rng(5)
+    dims = (200, 30, 20)
+    nnz = 3000
+    idx = np.stack([rng.integers(0, 50, nnz) * 4, rng.integers(0, 30, nnz), rng.integers(0, 20, nnz)]).astype(np.int64)
+    idx = np.concatenate([idx, idx[:, :100]], axis=1)
+    vals = np.concatenate([rng.integers(1, 4, nnz), rng.integers(1, 4, 100)]).astype(np.float64)
+    fs = synth.random_factors(dims, 4, 6)
+    lam = np.ones(4)
+    with cpapr.Tensor(dims, idx, vals, 4, tile_nnz=128) as t:
+        t.set_model(lam, fs)
+        for n in range(3):
+            want = oracle.phi(dims, idx, vals, fs, fs[n], n)
+            assert max_rel(t.phi(n), want) <= 1e-12
+
+
+@pytest.mark.parametrize("rank", [1, 3, 10, 33, 128])
+def test_ranks_not_power_of_two(rank):
+    T = synth.random_tensor((40, 30, 20), 4000, rank, 90 + rank)
+    lam, fs = model_for(T)
+    for prec, tol in [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)]:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, rank, precision=prec) as t:
+            t.set_model(lam, fs)
+            for n in range(3):
+                want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+                assert max_rel(t.phi(n), want) <= tol, (rank, prec, n)
+
+
+def test_invalid_inputs_are_errors_not_faults():
+    dims = (4, 3, 3)
+    idx = np.array([[0, 1, 3], [0, 2, 1], [1, 1, 2]], dtype=np.int64)
+    vals = np.array([1.0, 2.0, 3.0])
+    bad = idx.copy()
+    bad[1, 2] = 3
+    with pytest.raises(cpapr.CpaprError) as e:
+        cpapr.Tensor(dims, bad, vals, 2)
+    assert e.value.status == 2
+    bad = idx.copy()
+    bad[0, 0] = -1
+    with pytest.raises(cpapr.CpaprError) as e:
+        cpapr.Tensor(dims, bad, vals, 2)
+    assert e.value.status == 2
+    for v in (-1.0, np.nan, np.inf):
+        vv = vals.copy()
+        vv[1] = v
+        with pytest.raises(cpapr.CpaprError) as e:
+            cpapr.Tensor(dims, idx, vv, 2)
+        assert e.value.status == 3
+    with cpapr.Tensor(dims, idx, vals, 2) as t:
+        with pytest.raises(cpapr.CpaprError) as e:
+            t.phi(0)
+        assert e.value.status == 7
+        fs = synth.random_factors(dims, 2, 1)
+        fs[1][0, 0] = -0.5
+        with pytest.raises(cpapr.CpaprError) as e:
+            t.set_model(np.ones(2), fs)
+        assert e.value.status == 3
+        fs[1][0, 0] = 0.5
+        t.set_model(np.ones(2), fs)
+        with pytest.raises(cpapr.CpaprError) as e:
+            t.phi(3)
+        assert e.value.status == 1
+        t.phi(2)
