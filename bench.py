@@ -1,0 +1,470 @@
+#!/usr/bin/env python3
+"""CP-APR MU Phi^(n) throughput on GB300 (one JSON line on stdout).
+
+Workload (default): the 3-way 100,000 x 100,000 x 1,000 count tensor with
+10,000,000 distinct nonzeros, Zipf(1.2) coordinates in every mode, counts
+Poisson(2)+1, rank R = 32, seeded synthetic (a stand-in for the FROSTT
+tensors of the paper, which are not available here).
+
+One step = one outer iteration of Algorithm 1 over every mode (S and B, up to
+10 inner iterations of Phi with the KKT check and the multiplicative update,
+lambda normalisation) followed by the Poisson log-likelihood.  The unit is a
+nonzero visited by a Phi^(n) evaluation; `value` = Phi nonzero visits of all
+ranks / the slowest rank's device time for the K timed steps, with every
+other kernel of the step counted as overhead.  The per-mode layouts (480 MB
+of index and value streams) exceed the 129 MB L2, so no flush is needed
+between steps; the factor matrices stay L2-resident by design.
+
+Reported beside it: the FP32 form of the same step, the roofline of the
+dominant kernel (the Phi tile kernel), an end-to-end number through the C
+ABI from pinned host buffers, MTTKRP kernel throughput, the clocks seen
+during the timed region and the FP64 oracle timed on the host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  torchrun --nproc-per-node N bench.py --gpus N ...   (replicas: one per GPU)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Φ^(n) nonzeros/s and HBM GB/s (FP64 vs FP32 vs batched, 1 GB300)"
+UNIT = "nnz/s"
+TOL = 1e-4
+MAX_INNER = 10
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+# GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# random-row gather from an L2-resident table, 128-byte rows, measured on this GB300
+L2_GATHER_GBS = 7450.0
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    except OSError:
+        return dict(FALLBACK_PEAKS)
+
+
+# ---------------------------------------------------------------------------
+# byte and FLOP models (per Phi^(n) launch over the whole tensor)
+# ---------------------------------------------------------------------------
+
+def phi_bytes(dims, nnz, R, n, value_bytes, factor_bytes) -> float:
+    """Compulsory HBM bytes of one Phi^(n): the mode-n index and value streams,
+    the row offsets, one read of every other factor and of B, one write of Phi."""
+    N = len(dims)
+    other = sum(dims) - dims[n]
+    return nnz * (4 * (N - 1) + value_bytes) + 4 * (dims[n] + 1) + factor_bytes * R * (other + 2 * dims[n])
+
+
+def phi_flops(N, nnz, R) -> float:
+    """(N-2)R Khatri-Rao products, 2R dot, max + divide, 2R scale-add per nonzero."""
+    return nnz * ((N + 2) * R + 2)
+
+
+def phi_l2_bytes(N, nnz, R, factor_bytes) -> float:
+    """Factor-row bytes gathered per Phi^(n): N-1 other rows and the B row per nonzero."""
+    return nnz * N * R * factor_bytes
+
+
+# ---------------------------------------------------------------------------
+# multi-GPU plumbing (replicas)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, use_cuda: bool):
+    if dist is None:
+        return
+    if use_cuda:
+        import torch
+        dist.barrier(device_ids=[torch.cuda.current_device()])
+    else:
+        dist.barrier()
+
+
+def aggregate(dist, units: float, seconds: float, use_cuda: bool = False):
+    """Whole-job units (sum over ranks) and time (max over ranks)."""
+    if dist is None:
+        return units, seconds
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if use_cuda else torch.device("cpu")
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    s = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def gpu_selector() -> str | None:
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[0] if vis else None
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    from paper_2307_03276_gb300 import synth
+    spec = synth.SPECS[name]
+    T = synth.generate(spec)
+    lam = np.ones(T.rank)
+    fs = synth.random_factors(T.dims, T.rank, spec.seed + 17)
+    return T, lam, fs
+
+
+def cpu_baseline(T, lam, fs, seconds: float = 10.0, sample: int = 1_000_000) -> dict:
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    oracle.build()
+    S = min(sample, T.nnz)
+    idx = np.ascontiguousarray(T.idx[:, :S])
+    vals = np.ascontiguousarray(T.vals[:S])
+    done = 0
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.phi(T.dims, idx, vals, fs, fs[n] * lam[None, :], n)
+        done += S
+        n = (n + 1) % T.nmodes
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Phi^(n) over the first {S:,} of {T.nnz:,} nonzeros (random draw order), modes cycled, "
+                      f"{done // S} evaluations in {dt:.1f} s, FP64, Neumaier row sums"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def timed_solve(cp, torch, T, lam, fs, precision, steps, warmup, dist, use_cuda, clocks=None):
+    stream = torch.cuda.current_stream()
+    t = cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, profile=1, use_graph=0,
+                  stream=stream.cuda_stream)
+    t.set_model(lam, fs)
+    for _ in range(warmup):
+        t.mu_solve(TOL, 1, MAX_INNER, trace=True, ll_trace=False)
+    for k in range(7):
+        t.kernel_stats(k, reset=True)
+    launches0 = t.info().kernel_launches
+    inner = np.zeros(T.nmodes, dtype=np.int64)
+    barrier(dist, use_cuda)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        r = t.mu_solve(TOL, 1, MAX_INNER, trace=True, ll_trace=False)
+        inner += r["inner"].sum(axis=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier(dist, use_cuda)
+    ms = e0.elapsed_time(e1)
+    stats = {k: t.kernel_stats(k) for k in range(7)}
+    launches = t.info().kernel_launches - launches0
+    info = t.info()
+    # MTTKRP kernel time (outside the timed region)
+    for k in (cp.K_MTTKRP,):
+        t.kernel_stats(k, reset=True)
+    for n in range(T.nmodes):
+        t.mttkrp(n)
+    for n in range(T.nmodes):
+        t.mttkrp(n)
+    mt = t.kernel_stats(cp.K_MTTKRP)
+    t.close()
+    return {"ms": ms, "inner": inner, "stats": stats, "launches": launches, "clocks": clk, "info": info,
+            "mttkrp": mt, "last": r}
+
+
+def roofline_for(T, inner_per_mode, stats, precision, peaks, cp):
+    """Roofline of the Phi tile kernel from its measured average duration."""
+    N, nnz, R = T.nmodes, T.nnz, T.rank
+    fb = 8 if precision == cp.CPAPR_FP64 else 4
+    launches, total_ms = stats[cp.K_PHI]
+    byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb) for n in range(N))
+    fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R) for n in range(N))
+    l2 = sum(inner_per_mode[n] * phi_l2_bytes(N, nnz, R, fb) for n in range(N))
+    sec = total_ms / 1e3
+    hbm = {"achieved": byts / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    l2g = {"achieved": l2 / sec / 1e9, "peak": L2_GATHER_GBS, "unit": "GB/s"}
+    l2g["frac"] = l2g["achieved"] / l2g["peak"]
+    if precision == cp.CPAPR_FP64:
+        ach = fl / sec / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "phi_tile_kernel<double>", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
+                "frac": hbm["frac"], "traffic": None, "kernel": "phi_tile_kernel<float>",
+                "peak_source": f"{peaks['source']} hbm_gbs"}
+    roof["avg_launch_ms"] = total_ms / max(launches, 1)
+    roof["launches"] = launches
+    roof["hbm"] = hbm
+    roof["l2_gather"] = l2g
+    roof["flops_tflops"] = fl / sec / 1e12
+    return roof
+
+
+def e2e_run(cp, torch, T, lam, fs, precision, steps, warmup):
+    """Through the C ABI from pinned host buffers: create (H2D + index build),
+    set_model, one outer iteration + log-likelihood, get_model (D2H), destroy."""
+    stream = torch.cuda.current_stream()
+    idx_p = torch.from_numpy(T.idx).pin_memory()
+    val_p = torch.from_numpy(T.vals).pin_memory()
+    lam_p = torch.from_numpy(lam).pin_memory()
+    fs_p = [torch.from_numpy(np.ascontiguousarray(A)).pin_memory() for A in fs]
+    lam_o = torch.empty(T.rank, dtype=torch.float64).pin_memory()
+    fs_o = [torch.empty(A.shape, dtype=torch.float64).pin_memory() for A in fs]
+    opt = cp.cpapr_default_options(precision=precision, use_graph=0, stream=stream.cuda_stream)
+    rows = [idx_p[m] for m in range(T.nmodes)]
+    units = 0
+    launches = 0
+
+    def step():
+        nonlocal units, launches
+        ctx = cp.cpapr_create(T.dims, rows, val_p, T.rank, opt)
+        try:
+            cp.cpapr_set_model(ctx, lam_p, fs_p)
+            r = cp.cpapr_mu_solve(ctx, TOL, 1, MAX_INNER, trace=True, ll_trace=False)
+            import ctypes
+            arr = (ctypes.c_void_p * T.nmodes)(*[A.data_ptr() for A in fs_o])
+            cp._check(cp.load().cpapr_get_model(ctx, lam_o.data_ptr(), arr), ctx)
+            launches += cp.cpapr_get_info(ctx).kernel_launches
+            return int(r["inner"].sum()) * T.nnz
+        finally:
+            cp.cpapr_destroy(ctx)
+
+    for _ in range(warmup):
+        step()
+    units = 0
+    launches = 0
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        units += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h2d = T.idx.nbytes + T.vals.nbytes + lam.nbytes + sum(A.nbytes for A in fs)
+    d2h = lam.nbytes + sum(A.nbytes for A in fs)
+    return {"value": units / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": ms / steps, "gpu_launches_per_step": launches / max(steps, 1)}
+
+
+def run_ours(args):
+    import torch
+    from paper_2307_03276_gb300 import build, cpapr as cp
+    world, rank, local = dist_env()
+    use_cuda = torch.cuda.is_available()
+    if not use_cuda:
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = dist_init(world, use_cuda)
+    build.build()
+    peaks = load_peaks()
+    T, lam, fs = make_workload(args.workload)
+    prim = cp.CPAPR_FP64 if args.precision == "fp64" else cp.CPAPR_FP32
+    other = cp.CPAPR_FP32 if prim == cp.CPAPR_FP64 else cp.CPAPR_FP64
+    clocks = ClockSampler(gpu_selector())
+
+    res = timed_solve(cp, torch, T, lam, fs, prim, args.steps, args.warmup, dist, use_cuda, clocks)
+    units = float(res["inner"].sum()) * T.nnz
+    units_all, sec = aggregate(dist, units, res["ms"] / 1e3, use_cuda)
+    roof = roofline_for(T, res["inner"], res["stats"], prim, peaks, cp)
+    out = {"metric": METRIC, "value": units_all / sec, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prim == cp.CPAPR_FP64 else "f32",
+           "data": "synthetic (seeded Zipf/Poisson count tensor; FROSTT stand-in)",
+           "config": {"workload": T.name, "dims": list(T.dims), "nnz": T.nnz, "rank": T.rank,
+                      "precision": args.precision, "step": "1 outer MU iteration (all modes, <=10 inner) + loglik",
+                      "kkt_tol": TOL, "max_inner": MAX_INNER, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (mode layouts 480 MB > 129 MB), no flush",
+                      "graph": False, "tile_nnz": list(res["info"].tile_nnz)[:T.nmodes],
+                      "rank_lanes": list(res["info"].rank_lanes)[:T.nmodes]},
+           "roofline": roof, "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
+           "inner_iterations_per_mode": res["inner"].tolist()}
+    kern = {}
+    mt_l, mt_ms = res["mttkrp"]
+    kern["mttkrp_" + args.precision] = {"nnz_per_s": T.nnz * mt_l / (mt_ms / 1e3), "avg_launch_ms": mt_ms / max(mt_l, 1)}
+    if not args.no_variants:
+        r2 = timed_solve(cp, torch, T, lam, fs, other, args.steps, args.warmup, dist, use_cuda)
+        u2, s2 = aggregate(dist, float(r2["inner"].sum()) * T.nnz, r2["ms"] / 1e3, use_cuda)
+        name = "fp32" if other == cp.CPAPR_FP32 else "fp64"
+        out["variants"] = {name: {"value": u2 / s2, "unit": UNIT, "ms_per_step": s2 * 1e3 / args.steps,
+                                  "dtype": "f32" if other == cp.CPAPR_FP32 else "f64",
+                                  "roofline": roofline_for(T, r2["inner"], r2["stats"], other, peaks, cp),
+                                  "inner_iterations_per_mode": r2["inner"].tolist(),
+                                  "loglik_last": r2["last"]["loglik"]}}
+        mt_l, mt_ms = r2["mttkrp"]
+        kern["mttkrp_" + name] = {"nnz_per_s": T.nnz * mt_l / (mt_ms / 1e3), "avg_launch_ms": mt_ms / max(mt_l, 1)}
+    out["kernels"] = kern
+    if not args.no_e2e:
+        e2e = e2e_run(cp, torch, T, lam, fs, prim, max(2, args.steps // 2), 1)
+        ue, se = aggregate(dist, e2e["value"] * e2e["ms_per_step"] * max(2, args.steps // 2) / 1e3,
+                           e2e["ms_per_step"] * max(2, args.steps // 2) / 1e3, use_cuda)
+        e2e["value"] = ue / se
+        out["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(T, lam, fs, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, on bounded samples of the same workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    T, lam, fs = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    S = min(args.ref_sample, T.nnz)
+    idx = np.ascontiguousarray(T.idx[:, :S])
+    vals = np.ascontiguousarray(T.vals[:S])
+    for k in range(args.warmup):
+        n = k % T.nmodes
+        oracle.phi(T.dims, idx, vals, fs, fs[n] * lam[None, :], n)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        n = k % T.nmodes
+        oracle.phi(T.dims, idx, vals, fs, fs[n] * lam[None, :], n)
+    dt = time.perf_counter() - t0
+    value = S * args.steps / dt
+    sample = (f"each step: Phi^(n) (n cycling) over the first {S:,} of {T.nnz:,} nonzeros (random draw order) "
+              f"of the same tensor, FP64, single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Zipf/Poisson count tensor; FROSTT stand-in)",
+           "config": {"workload": T.name, "dims": list(T.dims), "nnz": T.nnz, "rank": T.rank, "precision": "fp64",
+                      "step": "Phi^(n) over a bounded sample", "parallelism": "host, 1 thread"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -213,6 +213,7 @@ typedef struct {
     int32_t ntiles[CPAPR_MAX_MODES];
     int32_t nsplit[CPAPR_MAX_MODES];      /* rows that span more than one tile */
     int64_t device_bytes;  /* device memory held by the context */
+    int64_t kernel_launches; /* kernels this context has launched (graph replays counted per kernel) */
 } cpapr_info;
 
 cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info);

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64), ("dims", ctypes.c_int64 * MAX_MODES),
                 ("tile_nnz", ctypes.c_int32 * MAX_MODES), ("rank_lanes", ctypes.c_int32 * MAX_MODES),
                 ("reduction", ctypes.c_int32 * MAX_MODES), ("ntiles", ctypes.c_int32 * MAX_MODES),
-                ("nsplit", ctypes.c_int32 * MAX_MODES), ("device_bytes", ctypes.c_int64)]
+                ("nsplit", ctypes.c_int32 * MAX_MODES), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -222,17 +223,22 @@ def cpapr_loglik(ctx) -> float:
     return v.value
 
 
-def cpapr_mu_solve(ctx, tol=1e-4, max_outer=10, max_inner=10, trace=False) -> dict:
+def cpapr_mu_solve(ctx, tol=1e-4, max_outer=10, max_inner=10, trace=False, ll_trace=None) -> dict:
+    """trace: also return the inner iterations per (outer, mode) and, unless
+    ll_trace is False, the log-likelihood after every outer iteration."""
+    if ll_trace is None:
+        ll_trace = trace
     res = Result()
     info = cpapr_get_info(ctx) if trace else None
     inner = np.zeros(max(max_outer, 1) * (info.nmodes if info else 1), dtype=np.int32) if trace else None
-    ll = np.zeros(max(max_outer, 1)) if trace else None
+    ll = np.zeros(max(max_outer, 1)) if ll_trace else None
     _check(load().cpapr_mu_solve(ctx, float(tol), int(max_outer), int(max_inner), ctypes.byref(res), _ptr(inner),
                                  _ptr(ll)), ctx)
     out = res.as_dict()
+    k = res.outer_iters
     if trace:
-        k = res.outer_iters
         out["inner"] = inner[:k * info.nmodes].reshape(k, info.nmodes)
+    if ll_trace:
         out["loglik_trace"] = ll[:k]
     return out
 
@@ -304,8 +310,8 @@ class Tensor:
     def loglik(self) -> float:
         return cpapr_loglik(self.ctx)
 
-    def mu_solve(self, tol=1e-4, max_outer=10, max_inner=10, trace=False) -> dict:
-        return cpapr_mu_solve(self.ctx, tol, max_outer, max_inner, trace)
+    def mu_solve(self, tol=1e-4, max_outer=10, max_inner=10, trace=False, ll_trace=None) -> dict:
+        return cpapr_mu_solve(self.ctx, tol, max_outer, max_inner, trace, ll_trace)
 
     def info(self) -> Info:
         return cpapr_get_info(self.ctx)

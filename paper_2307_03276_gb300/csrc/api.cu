@@ -45,6 +45,15 @@ cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes) {
     return CPAPR_OK;
 }
 
+void count_launch(cpapr_ctx *ctx, int k) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        ctx->graph_capture_kernels += k;
+        return;
+    }
+    ctx->launches += k;
+}
+
 ProfScope::ProfScope(cpapr_ctx *c, int k) : ctx(c), kind(k) {
     if (!ctx->opt.profile) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -438,6 +447,7 @@ cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info) {
         info->nsplit[m] = ctx->mode[m].nsplit;
     }
     info->device_bytes = ctx->device_bytes;
+    info->kernel_launches = ctx->launches;
     return CPAPR_OK;
 }
 

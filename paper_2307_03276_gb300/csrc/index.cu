@@ -107,11 +107,13 @@ cpapr_status exclusive_scan_u32(cpapr_ctx *ctx, uint32_t *data, int64_t n, uint3
     if (nb > 1) {
         CPAPR_CUDA(ctx, cudaMallocAsync((void **)&bs, nb * 4, ctx->stream));
         scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(data, n, bs);
+        count_launch(ctx);
         CPAPR_CUDA(ctx, cudaGetLastError());
         cpapr_status st = exclusive_scan_u32(ctx, bs, nb, nullptr);
         if (st != CPAPR_OK) return st;
     }
     scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(data, n, bs, total_out_dev);
+    count_launch(ctx);
     CPAPR_CUDA(ctx, cudaGetLastError());
     if (bs) CPAPR_CUDA(ctx, cudaFreeAsync(bs, ctx->stream));
     return CPAPR_OK;
@@ -227,6 +229,7 @@ static cpapr_status radix_sort(cpapr_ctx *ctx, uint32_t *keys, uint32_t *vals, u
         CPAPR_CUDA(ctx, cudaGetLastError());
         CPAPR_TRY(exclusive_scan_u32(ctx, counts, (int64_t)256 * ntiles, nullptr));
         rs_scatter_kernel<<<ntiles, kRsThreads, 0, ctx->stream>>>(ka, va, kb, vb, n, shift, counts, ntiles);
+        count_launch(ctx, 2);
         CPAPR_CUDA(ctx, cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -318,12 +321,14 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         if (nnz > 0) {
             BL_CUDA(cudaMemcpyAsync(stage, idx_in[m], nnz * 8, cudaMemcpyDefault, s));
             narrow_check_kernel<<<grid_for(nnz), 256, 0, s>>>(stage, nnz, ctx->dims[m], idx32[m], ctx->errflag);
+            count_launch(ctx);
             BL_CUDA(cudaGetLastError());
         }
     }
     if (nnz > 0) {
         BL_CUDA(cudaMemcpyAsync(vals, vals_in, nnz * 8, cudaMemcpyDefault, s));
         check_values_kernel<<<grid_for(nnz), 256, 0, s>>>(vals, nnz, ctx->errflag);
+        count_launch(ctx);
         BL_CUDA(cudaGetLastError());
     }
     int32_t hflag[4] = {0, 0, 0, 0};
@@ -368,6 +373,7 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         }
         BL_CUDA(cudaMemcpyAsync(keys, idx32[n], nnz * 4, cudaMemcpyDeviceToDevice, s));
         iota_kernel<<<grid_for(nnz), 256, 0, s>>>(perm, nnz);
+        count_launch(ctx, 2 + ctx->N);  // iota, seg, N-1 index gathers, value gather
         BL_CUDA(cudaGetLastError());
         int bits = 0;
         while (bits < 31 && ((int64_t)1 << bits) < (int64_t)L.In) ++bits;
@@ -476,6 +482,7 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     const int nt = L.ntiles;
     CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_first, (size_t)std::max(nt, 1) * 4, s));
     CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_lo, (size_t)(nt + 1) * 4, s));
+    count_launch(ctx, nt >= 2 ? 3 : 1);
     tile_rows_kernel<<<(unsigned)ceil_div(nt + 1, 256), 256, 0, s>>>(L.seg, L.In, ctx->nnz, tile_nnz, nt, L.row_first,
                                                                      L.row_lo);
     CPAPR_CUDA(ctx, cudaGetLastError());

@@ -90,6 +90,9 @@ struct cpapr_ctx {
     bool sticky = false;
     std::string err;
     int64_t device_bytes = 0;
+    int64_t launches = 0;         // kernels launched (see count_launch)
+    int graph_body_kernels[CPAPR_MAX_MODES] = {};
+    int graph_capture_kernels = 0;  // kernels recorded by the capture in progress
     std::vector<void *> allocs;
     // profiling
     std::vector<cudaEvent_t> ev_pool;
@@ -123,6 +126,10 @@ cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what);
     } while (0)
 
 cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes);
+
+// Counts kernel launches; launches recorded while a stream capture is active
+// are not counted here (graph replays are counted from the iterations run).
+void count_launch(cpapr_ctx *ctx, int k = 1);
 
 // ---- profiling ------------------------------------------------------------
 struct ProfScope {

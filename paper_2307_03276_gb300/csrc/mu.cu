@@ -49,6 +49,7 @@ __global__ void sb_kernel(const T *__restrict__ A, const T *__restrict__ phi_pre
 cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner) {
     const int64_t rows = ctx->dims[n];
     ProfScope ps(ctx, K_SB);
+    count_launch(ctx);
     if (ctx->esize == 8)
         sb_kernel<double><<<grid_for(rows * ctx->Rp), 256, 0, ctx->stream>>>(
             (const double *)ctx->A[n], (const double *)ctx->Phi[n], ctx->lambda, (double *)ctx->B, rows, ctx->Rp,
@@ -112,6 +113,7 @@ cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, Inn
                            unsigned long long cond_handle, int use_cond) {
     const int64_t nel = ctx->dims[n] * ctx->Rp;
     ProfScope ps(ctx, K_UPDATE);
+    count_launch(ctx);
     const unsigned g = grid_for(nel, 256, 152 * 4);
     if (ctx->esize == 8)
         update_kernel<double><<<g, 256, 0, ctx->stream>>>((double *)ctx->B, (const double *)ctx->Phi[n], nel, inner,
@@ -178,6 +180,7 @@ cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
     const int Rp = ctx->Rp;
     const int parts = colsum_parts(rows, Rp);
     ProfScope ps(ctx, K_NORM);
+    count_launch(ctx, 2);
     if (ctx->esize == 8) {
         colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->B, rows, Rp, ctx->colpart);
         normalise_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
@@ -202,6 +205,7 @@ __global__ void scale_b_kernel(const T *__restrict__ A, const double *__restrict
 }
 
 cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB) {
+    count_launch(ctx);
     const int64_t nel = ctx->dims[n] * ctx->Rp;
     if (ctx->esize == 8)
         scale_b_kernel<double><<<grid_for(nel), 256, 0, ctx->stream>>>((const double *)ctx->A[n], ctx->lambda,
@@ -236,6 +240,7 @@ cpapr_status launch_colsums(cpapr_ctx *ctx) {
             colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->A[m], rows, Rp,
                                                                           ctx->colpart);
         reduce_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->colpart, parts, Rp, ctx->colsum + (int64_t)m * Rp);
+        count_launch(ctx, 2);
         CPAPR_CUDA(ctx, cudaGetLastError());
     }
     return CPAPR_OK;
@@ -257,6 +262,7 @@ __global__ void ll_finish_kernel(const double *__restrict__ lambda, const double
 cpapr_status launch_ll_finish(cpapr_ctx *ctx, double *dst) {
     CPAPR_TRY(launch_colsums(ctx));
     ll_finish_kernel<<<1, 32, 0, ctx->stream>>>(ctx->lambda, ctx->colsum, ctx->N, ctx->Rp, dst);
+    count_launch(ctx);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
 }
@@ -311,6 +317,7 @@ __global__ void fill_lambda_kernel(double *__restrict__ lambda, int R, int Rp) {
 cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed) {
     const int Rp = ctx->Rp;
     fill_lambda_kernel<<<1, 256, 0, ctx->stream>>>(ctx->lambda, ctx->R, Rp);
+    count_launch(ctx, 1 + 3 * ctx->N);
     CPAPR_CUDA(ctx, cudaGetLastError());
     for (int m = 0; m < ctx->N; ++m) {
         const int64_t rows = ctx->dims[m];
@@ -356,6 +363,7 @@ cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void
     if (rows > 0)
         CPAPR_CUDA(ctx, cudaMemcpy2DAsync(ctx->stage, (size_t)Rp * 8, src, (size_t)R * 8, (size_t)R * 8, (size_t)rows,
                                           cudaMemcpyDefault, ctx->stream));
+    count_launch(ctx);
     if (ctx->esize == 8)
         convert_kernel<double><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (double *)dst, n, ctx->errflag);
     else
@@ -370,6 +378,7 @@ cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, doub
     const double *from = (const double *)src;
     if (ctx->esize != 8) {
         widen_kernel<float><<<grid_for(n), 256, 0, ctx->stream>>>((const float *)src, ctx->stage, n);
+        count_launch(ctx);
         CPAPR_CUDA(ctx, cudaGetLastError());
         from = ctx->stage;
     }

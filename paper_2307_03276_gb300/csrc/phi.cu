@@ -111,15 +111,18 @@ cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *ou
     if (ctx->nnz > 0) {
         ProfScope ps(ctx, op == OP_MTTKRP ? K_MTTKRP : K_PHI);
         cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, op);
+        count_launch(ctx);
         if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "phi tile kernel");
     }
     if (ctx->nnz > 0 && !atomic && L.nsplit > 0) {
         ProfScope ps(ctx, K_FIXUP);
+        count_launch(ctx);
         cudaError_t e = ctx->esize == 8 ? run_fixup<double>(a, op, ctx->stream) : run_fixup<float>(a, op, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "phi fix-up kernel");
     }
     if (op == OP_PHI && inner && (atomic || ctx->nnz == 0)) {
+        count_launch(ctx);
         cudaError_t e = ctx->esize == 8
                             ? run_kkt_rows<double>((const double *)B, (const double *)out, nel, inner, ctx->stream)
                             : run_kkt_rows<float>((const float *)B, (const float *)out, nel, inner, ctx->stream);
@@ -155,6 +158,7 @@ cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst) {
         cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_LL);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "log-likelihood kernel");
         sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->llpart, L.ntiles, dst);
+        count_launch(ctx, 2);
         CPAPR_CUDA(ctx, cudaGetLastError());
     }
     return CPAPR_OK;

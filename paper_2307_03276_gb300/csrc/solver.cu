@@ -57,8 +57,10 @@ static cpapr_status build_inner_graph(cpapr_ctx *ctx, int n, double tol, int max
         return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph");
     }
     InnerState *inner = ctx->inner + n;
+    ctx->graph_capture_kernels = 0;
     cpapr_status st = launch_phi(ctx, n, OP_PHI, ctx->B, ctx->Phi[n], inner);
     if (st == CPAPR_OK) st = launch_update(ctx, n, tol, max_inner, inner, (unsigned long long)h, 1);
+    ctx->graph_body_kernels[n] = ctx->graph_capture_kernels;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(ctx->stream, &captured);
     if (st != CPAPR_OK) {
@@ -124,6 +126,7 @@ cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, 
         double kmax = 0.0;
         for (int n = 0; n < N; ++n) {
             total_inner += hs[n].used;
+            if (ctx->opt.use_graph) ctx->launches += (int64_t)hs[n].used * ctx->graph_body_kernels[n];
             if (!(hs[n].passed && hs[n].used == 1)) all_first = false;
             kmax = std::max(kmax, hs[n].viol);
             if (inner_trace) inner_trace[(int64_t)k * N + n] = hs[n].used;
@@ -182,6 +185,7 @@ cpapr_status batch_mu_solve(cpapr_ctx *const *ctxs, int count, double tol, int m
             double kmax = 0.0;
             for (int n = 0; n < c->N; ++n) {
                 tr[i].total += hs[i][n].used;
+                if (c->opt.use_graph) c->launches += (int64_t)hs[i][n].used * c->graph_body_kernels[n];
                 if (!(hs[i][n].passed && hs[i][n].used == 1)) all_first = false;
                 kmax = std::max(kmax, hs[i][n].viol);
             }

@@ -1,0 +1,53 @@
+"""Host logic of bench.py: byte/FLOP models and the multi-rank aggregation
+(world size 2 over gloo on CPU, the same code path NCCL takes on GPUs)."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def test_byte_model_matches_hand_count():
+    # 4-way 200,000 x 200,000 x 10,000 x 365, 5e7 nonzeros, R = 16, FP64, mode 0:
+    # 5e7*(12+8) + 4*(2e5+1) + 8*16*(2e5+1e4+365 + 2*2e5) = 1.0789 GB
+    b = bench.phi_bytes((200_000, 200_000, 10_000, 365), 50_000_000, 16, 0, 8, 8)
+    assert b == 50_000_000 * 20 + 4 * 200_001 + 8 * 16 * (210_365 + 400_000)
+    assert abs(b / 1e9 - 1.0789) < 1e-3
+    assert bench.phi_flops(4, 10, 16) == 10 * (6 * 16 + 2)
+    assert bench.phi_l2_bytes(3, 10, 32, 4) == 10 * 3 * 32 * 4
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    d = bench.dist_init(world, use_cuda=False)
+    bench.barrier(d, use_cuda=False)
+    u, s = bench.aggregate(d, units=100.0 * (rank + 1), seconds=0.5 + rank, use_cuda=False)
+    q.put((rank, u, s))
+    dist.destroy_process_group()
+
+
+def test_aggregate_two_ranks_gloo():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    procs = [mp.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, u, s in got:
+        assert u == 300.0 and s == 1.5
