@@ -147,6 +147,34 @@ cpapr_status cpapr_get_model(cpapr_ctx *ctx, double *lambda, double *const *fact
  */
 cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *out);
 
+/* Size of the fixed device scratch used by cpapr_phi_noalloc (8 MiB). */
+#define CPAPR_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * Phi^(mode) like cpapr_phi, for callers that cannot have the library
+ * allocate device memory during the call: for example code whose device
+ * memory is held by another allocator (a framework's caching allocator that
+ * has reserved the GPU, a fixed memory budget) or a loop that must not block
+ * on cudaMalloc/cudaFree.  The paper has no counterpart; it is a deployment
+ * variant of Algorithm 2.
+ *  B    NULL (B = A^(mode) diag(lambda)) or a DEVICE pointer, I_mode x R doubles.
+ *  out  DEVICE pointer receiving I_mode x R doubles.
+ * The kernel's scratch (per-tile partial rows, 2 x tiles x padded rank
+ * elements) comes from a fixed array of CPAPR_NOALLOC_SCRATCH_BYTES in device
+ * memory that every GPU loading the library holds until the process exits;
+ * the call performs no cudaMalloc, cudaFree or other allocating call.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU --
+ * on other streams, contexts or host threads -- race and must be serialised
+ * by the caller.
+ * Errors: E_RANGE when the mode needs more scratch than the array holds
+ * (raise tile_nnz or use cpapr_phi), E_ARG for host pointers or a bad mode,
+ * E_STATE without a model, E_CUDA.
+ */
+cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const double *B, double *out);
+
 /*
  * MTTKRP of the paper's Experiment 8: M[i_n,:] = sum over entries in slice
  * i_n of x * (elementwise product of A^(m)[i_m,:], m != n), i.e.

@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
     lib.cpapr_init_random.argtypes = [P, ctypes.c_uint64]
     lib.cpapr_get_model.argtypes = [P, P, P]
     lib.cpapr_phi.argtypes = [P, i32, P, P]
+    lib.cpapr_phi_noalloc.argtypes = [P, i32, P, P]
     lib.cpapr_mttkrp.argtypes = [P, i32, P]
     lib.cpapr_loglik.argtypes = [P, P]
     lib.cpapr_mu_solve.argtypes = [P, f64, i32, i32, ctypes.POINTER(Result), P, P]
@@ -93,6 +94,7 @@ def load() -> ctypes.CDLL:
     lib.cpapr_version.argtypes = []
     lib.cpapr_version.restype = ctypes.c_char_p
     for name in ("cpapr_create", "cpapr_set_model", "cpapr_init_random", "cpapr_get_model", "cpapr_phi",
+                 "cpapr_phi_noalloc",
                  "cpapr_mttkrp", "cpapr_loglik", "cpapr_mu_solve", "cpapr_batch_mu_solve", "cpapr_get_info",
                  "cpapr_kernel_stats"):
         getattr(lib, name).restype = ctypes.c_int
@@ -208,6 +210,18 @@ def cpapr_phi(ctx, mode: int, B=None, out=None):
     out = _out_matrix(ctx, mode, out)
     Bc = _as_f64(B) if B is not None else None
     _check(load().cpapr_phi(ctx, int(mode), _ptr(Bc), _ptr(out)), ctx)
+    return out
+
+
+def cpapr_phi_noalloc(ctx, mode: int, out, B=None):
+    """Phi^(mode) into the device buffer `out` (I_mode x R float64, e.g. a CUDA
+    torch tensor) without any device allocation inside the call: the kernel's
+    scratch comes from a fixed array the library carries on every GPU.  For
+    callers that cannot let the library call cudaMalloc (memory owned by
+    another allocator, loops that must not block on allocation).  B, if
+    given, is a device buffer too.  Overlapping calls share that scratch and
+    race; make the first call on a device before any stream capture."""
+    _check(load().cpapr_phi_noalloc(ctx, int(mode), _ptr(B), _ptr(out)), ctx)
     return out
 
 

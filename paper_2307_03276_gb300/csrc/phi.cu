@@ -131,6 +131,27 @@ cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *ou
     return CPAPR_OK;
 }
 
+// Phi^(n) with the segmented reduction and a caller-supplied carry buffer
+// (2 x ntiles x Rp elements of the working type).  Launches kernels only:
+// no allocation, no event, no memset.
+cpapr_status launch_phi_given_carry(cpapr_ctx *ctx, int n, const void *B, void *out, void *carry) {
+    ModeLayout &L = ctx->mode[n];
+    PhiArgs a = make_args(ctx, n, B, out, nullptr);
+    a.atomic = 0;
+    a.carry = carry;
+    if (ctx->nnz == 0) return fail(ctx, CPAPR_E_ARG, "empty tensor");
+    cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_PHI);
+    count_launch(ctx);
+    if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "phi tile kernel");
+    if (L.nsplit > 0) {
+        e = ctx->esize == 8 ? run_fixup<double>(a, OP_PHI, ctx->stream) : run_fixup<float>(a, OP_PHI, ctx->stream);
+        count_launch(ctx);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "phi fix-up kernel");
+    }
+    return CPAPR_OK;
+}
+
 __global__ void sum_parts_kernel(const double *__restrict__ part, int n, double *__restrict__ dst) {
     // one block, fixed order: per-thread strided sums, then a tree
     __shared__ double sm[256];
