@@ -411,6 +411,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_only(args):
+    """Phi^(n) for every mode, `steps` rounds: a small target for ncu captures."""
+    import torch
+    from paper_2307_03276_gb300 import build, cpapr as cp
+    torch.cuda.set_device(0)
+    build.build()
+    T, lam, fs = make_workload(args.workload)
+    prec = cp.CPAPR_FP64 if args.precision == "fp64" else cp.CPAPR_FP32
+    with cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=prec, profile=1, use_graph=0) as t:
+        t.set_model(lam, fs)
+        for _ in range(args.steps):
+            for n in range(T.nmodes):
+                t.phi(n)
+        launches, ms = t.kernel_stats(cp.K_PHI)
+        info = t.info()
+    print(json.dumps({"kernel": "phi_tile_kernel", "precision": args.precision, "workload": T.name,
+                      "launches": launches, "avg_ms": ms / max(launches, 1),
+                      "tile_nnz": list(info.tile_nnz)[:T.nmodes], "rank_lanes": list(info.rank_lanes)[:T.nmodes]}))
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores, on bounded samples of the same workload."""
     world, rank, _ = dist_env()
@@ -457,7 +477,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only run Phi^(n) for every mode --steps times (profiling target)")
     args = ap.parse_args(argv)
+    if args.kernel_only:
+        run_kernel_only(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
