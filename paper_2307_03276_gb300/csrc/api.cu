@@ -103,15 +103,16 @@ static int next_pow2(int v) {
     return p;
 }
 
-// Built-in choice of lanes per nonzero and nonzeros per tile.
-// FP64: one lane per nonzero up to 16 ranks (no redundant division or
-// shuffle adds on the scarce FP64 pipe); FP32: 16-byte vectors of 4 ranks
-// per lane up to 32 ranks, 8 ranks per lane above.
+// Built-in choice of lanes per nonzero and nonzeros per tile (from sweeps on
+// GB300).  FP64: one lane per nonzero up to 16 ranks (no shuffle adds on the
+// scarce FP64 pipe), 16 ranks per lane above with batches of two nonzeros, so
+// that every nonzero still costs one division; FP32: 16-byte vectors of 4
+// ranks per lane up to 32 ranks, 8 ranks per lane above.
 static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
     const int Rp = ctx->Rp;
     int g;
     if (ctx->esize == 8)
-        g = std::max(1, Rp / 16);
+        g = Rp <= 16 ? 1 : Rp / 16;
     else
         g = Rp <= 32 ? std::max(1, Rp / 4) : Rp / 8;
     *lanes = g;

@@ -18,11 +18,18 @@ namespace cpapr {
 
 namespace {
 constexpr int kThreads = sizeof(PHI_T) == 8 ? 128 : 256;
-constexpr int kUnroll = sizeof(PHI_T) == 8 ? 1 : 2;
+// nonzeros per batch (U <= G when G > 1: after the reduce-scatter every lane
+// finishes one of them, so a nonzero costs G / U divisions).  FP64 at 16
+// ranks per lane has no registers to spare for a second batch entry.
+template <int RPL, int G>
+constexpr int unroll_for() {
+    if (sizeof(PHI_T) == 8) return RPL >= 32 ? 1 : (G >= 2 ? 2 : 1);
+    return G >= 4 ? 4 : 2;
+}
 
 template <int RPL, int G, int OP>
 cudaError_t run(const PhiArgs &a, cudaStream_t s) {
-    auto k = phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, kUnroll>;
+    auto k = phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, unroll_for<RPL, G>()>;
     size_t smem = 0;
     if (OP != OP_LL && !a.atomic) smem = (size_t)2 * kThreads * RPL * sizeof(PHI_T) + (size_t)2 * (kThreads / G) * 4;
     if (smem > 48 * 1024) {
@@ -47,10 +54,13 @@ cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s)
     CPAPR_CASE(4, 1)
     CPAPR_CASE(8, 1)
     CPAPR_CASE(16, 1)
+    CPAPR_CASE(32, 1)
     CPAPR_CASE(8, 2)
     CPAPR_CASE(16, 2)
+    CPAPR_CASE(32, 2)
     CPAPR_CASE(8, 4)
     CPAPR_CASE(16, 4)
+    CPAPR_CASE(32, 4)
     CPAPR_CASE(16, 8)
 #else
     CPAPR_CASE(4, 1)

@@ -92,10 +92,43 @@ template <> struct KSum<float> {
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
-template <typename T> __device__ __forceinline__ double row_violation(T b, T phi) {
-    double bb = (double)b, pp = (double)phi;
-    double m = bb < 1.0 - pp ? bb : 1.0 - pp;
-    return fabs(m);
+// |min(B, 1 - Phi)| in the working precision.  Its maximum is exact in any
+// precision; only 1 - Phi rounds, which is far below any KKT tolerance.
+template <typename T> __device__ __forceinline__ T viol_t(T b, T phi) {
+    const T om = T(1) - phi;
+    const T m = b < om ? b : om;
+    return m < T(0) ? -m : m;
+}
+
+// x / max(s, eps): IEEE division in FP64; the fast reciprocal-based division
+// in FP32 (within 2 ulp, far inside the FP32 path's 1e-5 tolerance).
+__device__ __forceinline__ double phi_divide(double x, double m) { return x / m; }
+__device__ __forceinline__ float phi_divide(float x, float m) { return __fdividef(x, m); }
+
+// On entry each of the G lanes of a group holds U partial dot products (its
+// RPL ranks) of the group's U nonzeros.  A reduce-scatter halves the set at
+// every exchange, so that afterwards lane l holds the complete sum for
+// nonzero u = l / (G / U) -- each lane divides once per batch instead of U
+// times.  Requires U <= G (G > 1).
+template <typename T, int G, int U>
+__device__ __forceinline__ T group_reduce_scatter(T (&s)[U], int lane, unsigned gmask) {
+    static_assert(U <= G, "reduce-scatter needs U <= G");
+    int o = G / 2;
+#pragma unroll
+    for (int h = U / 2; h >= 1; h >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = upper ? s[i] : s[i + h];
+            const T keep = upper ? s[i + h] : s[i];
+            s[i] = keep + __shfl_xor_sync(gmask, send, o);
+        }
+        o >>= 1;
+    }
+    T tot = s[0];
+#pragma unroll
+    for (int oo = G / (2 * U); oo > 0; oo >>= 1) tot += __shfl_xor_sync(gmask, tot, oo);
+    return tot;
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -109,7 +142,7 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Reduces the block's violation and publishes it into inner->kkt[l & 1].
+// Reduces the block's violation (in FP64) and publishes it into inner->kkt[l & 1].
 template <int THREADS>
 __device__ __forceinline__ void publish_kkt(double v, InnerState *inner, double *sm) {
     v = warp_max(v);
@@ -175,6 +208,48 @@ __device__ __forceinline__ void mul_row(const T *__restrict__ base, T (&dst)[RPL
     }
 }
 
+// <row at base, v> with the row read through L1 (used by the FP64 kernels
+// where registers are short; one FMA chain, see dot_regs)
+template <typename T, int RPL>
+__device__ __forceinline__ T dot_global(const T *__restrict__ base, const T (&v)[RPL]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    const V *p = reinterpret_cast<const V *>(base);
+    T d = T(0);
+#pragma unroll
+    for (int k = 0; k < RPL / VN; ++k) {
+        V x = __ldg(p + k);
+        if constexpr (VN == 4) {
+            d = fma(x.x, v[4 * k + 0], d);
+            d = fma(x.y, v[4 * k + 1], d);
+            d = fma(x.z, v[4 * k + 2], d);
+            d = fma(x.w, v[4 * k + 3], d);
+        } else {
+            d = fma(x.x, v[2 * k + 0], d);
+            d = fma(x.y, v[2 * k + 1], d);
+        }
+    }
+    return d;
+}
+
+// <a, b>.  FP32: four independent partial sums (short dependency chains);
+// FP64: one chain, because on this GPU the FP64 pipe itself is the limit
+// and every extra add costs a pipe slot.
+template <typename T, int RPL>
+__device__ __forceinline__ T dot_regs(const T (&a)[RPL], const T (&b)[RPL]) {
+    if constexpr (RPL < 4 || sizeof(T) == 8) {
+        T d = T(0);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) d = fma(a[r], b[r], d);
+        return d;
+    } else {
+        T d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) d[r & 3] = fma(a[r], b[r], d[r & 3]);
+        return (d[0] + d[1]) + (d[2] + d[3]);
+    }
+}
+
 template <typename T, int RPL>
 __device__ __forceinline__ void store_row(T *__restrict__ base, const T (&src)[RPL]) {
     using V = typename Vec16<T>::type;
@@ -235,8 +310,17 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     T *__restrict__ out = reinterpret_cast<T *>(a.out);
     const T eps = (T)a.eps;
 
-    double kkt = 0.0;
+    T kkt = T(0);
     double ll = 0.0;
+    // with G > 1 lanes each lane finishes one nonzero of the batch: u_mine
+    constexpr int LPU = G > 1 ? G / U : 1;  // lanes per nonzero after the reduce-scatter
+    const int u_mine = G > 1 ? lane / LPU : 0;
+    const int gbase = (wlane / G) * G;
+    // B rows held in registers (reused along a row), except for wide FP64
+    // lanes, whose registers go to the Khatri-Rao row and the accumulator:
+    // there the dot reads the B row through L1 for every nonzero
+    constexpr bool BREG = !(sizeof(T) == 8 && RPL >= 16);
+    constexpr int BR = BREG ? RPL : 1;
 
     if (ga < gb) {
         int32_t row = ub_seg(seg, a.row_first[t], a.row_lo[t + 1], ga) - 1;
@@ -247,19 +331,26 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
         KSum<T> acc[RPL];
 #pragma unroll
         for (int r = 0; r < RPL; ++r) acc[r].zero();
-        T brow[RPL];
+        T brow[BR];  // B row of `cur` (loaded once per row, not per nonzero)
+        int32_t brow_row = -1;
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) brow[r] = T(0);
+        for (int r = 0; r < BR; ++r) brow[r] = T(0);
 
-        auto flush = [&](int32_t frow, int64_t fbeg, int64_t fend) {
+        auto flush = [&](int32_t frow, int64_t fbeg, int64_t fend, const T(&bq)[BR]) {
             T v[RPL];
 #pragma unroll
             for (int r = 0; r < RPL; ++r) v[r] = acc[r].value();
             if (fbeg >= ga && fend <= gb) {
                 store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
                 if (OP == OP_PHI) {
+                    if constexpr (BREG) {
 #pragma unroll
-                    for (int r = 0; r < RPL; ++r) kkt = fmax(kkt, row_violation(brow[r], v[r]));
+                        for (int r = 0; r < RPL; ++r) kkt = tmax(kkt, viol_t(bq[r], v[r]));
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r)
+                            kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)frow * Rp + col0 + r), v[r]));
+                    }
                 }
             } else if (a.atomic) {
 #pragma unroll
@@ -292,56 +383,96 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
                 rb[u] = rbeg;
                 re[u] = rend;
             }
+            // gathers of the batch: Khatri-Rao rows, and a B row only where the row changes
             T pi[U][RPL];
-            T bb[U][RPL];
+            T bb[U][BR];
+            bool newb[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 load_row<T, RPL>(reinterpret_cast<const T *>(a.A[0]) + (int64_t)ii[u][0] * Rp + col0, pi[u]);
 #pragma unroll
                 for (int k = 1; k < MAXK; ++k)
                     if (k < nm1) mul_row<T, RPL>(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[u][k] * Rp + col0, pi[u]);
-                if (OP != OP_MTTKRP) load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, bb[u]);
+                if (OP != OP_MTTKRP && BREG) {
+                    newb[u] = rr[u] != (u == 0 ? brow_row : rr[u > 0 ? u - 1 : 0]);
+                    if (newb[u]) load_row<T, BR>(Bm + (int64_t)rr[u] * Rp + col0, bb[u]);
+                }
             }
+            T v[U];
+            if (OP == OP_MTTKRP) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (q + u < gb) {
-                    if (OP != OP_LL && rr[u] != cur) {
-                        flush(cur, cbeg, cend);
-                        cur = rr[u];
-                        cbeg = rb[u];
-                        cend = re[u];
+                for (int u = 0; u < U; ++u) v[u] = xx[u];
+            } else {
+                T s[U];
 #pragma unroll
-                        for (int r = 0; r < RPL; ++r) acc[r].zero();
-                    }
-                    if (OP == OP_MTTKRP) {
+                for (int u = 0; u < U; ++u) {
+                    if constexpr (BREG) {
+                        if (!newb[u]) {
 #pragma unroll
-                        for (int r = 0; r < RPL; ++r) acc[r].fma_add(xx[u], pi[u][r]);
-                    } else {
-                        T s = T(0);
-#pragma unroll
-                        for (int r = 0; r < RPL; ++r) s = fma(bb[u][r], pi[u][r], s);
-#pragma unroll
-                        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
-                        if (OP == OP_PHI) {
-                            const T v = xx[u] / tmax(s, eps);
-#pragma unroll
-                            for (int r = 0; r < RPL; ++r) {
-                                acc[r].fma_add(v, pi[u][r]);
-                                brow[r] = bb[u][r];
-                            }
-                        } else {  // OP_LL: x log(m) with m = <lambda o A^(n)[i_n], pi>
-                            if (lane == 0) {
-                                if constexpr (sizeof(T) == 8)
-                                    ll += (double)xx[u] * log((double)s);
-                                else
-                                    ll += (double)xx[u] * (double)logf((float)s);
-                            }
+                            for (int r = 0; r < BR; ++r) bb[u][r] = u == 0 ? brow[r] : bb[u > 0 ? u - 1 : 0][r];
                         }
+                        if constexpr (BR == RPL) s[u] = dot_regs<T, RPL>(bb[u], pi[u]);
+                    } else {
+                        s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
+                    }
+                }
+                if constexpr (G == 1) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (OP == OP_PHI) {
+                            v[u] = phi_divide(xx[u], tmax(s[u], eps));
+                        } else if (q + u < gb) {  // OP_LL: x log(m), m = <lambda o A^(n)[i_n], pi>
+                            if constexpr (sizeof(T) == 8)
+                                ll += (double)xx[u] * log((double)s[u]);
+                            else
+                                ll += (double)xx[u] * (double)logf((float)s[u]);
+                        }
+                    }
+                } else {
+                    const T tot = group_reduce_scatter<T, G, U>(s, lane, gmask);
+                    T xm = xx[0];
+#pragma unroll
+                    for (int u = 1; u < U; ++u)
+                        if (u_mine == u) xm = xx[u];
+                    if (OP == OP_PHI) {
+                        const T vm = phi_divide(xm, tmax(tot, eps));
+#pragma unroll
+                        for (int u = 0; u < U; ++u) v[u] = __shfl_sync(gmask, vm, gbase + u * LPU);
+                    } else if (q + u_mine < gb && (lane % LPU) == 0) {
+                        if constexpr (sizeof(T) == 8)
+                            ll += (double)xm * log((double)tot);
+                        else
+                            ll += (double)xm * (double)logf((float)tot);
                     }
                 }
             }
+            if (OP != OP_LL) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (q + u < gb) {
+                        if (rr[u] != cur) {
+                            if (u == 0)
+                                flush(cur, cbeg, cend, brow);
+                            else
+                                flush(cur, cbeg, cend, bb[u > 0 ? u - 1 : 0]);
+                            cur = rr[u];
+                            cbeg = rb[u];
+                            cend = re[u];
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r) acc[r].zero();
+                        }
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) acc[r].fma_add(v[u], pi[u][r]);
+                    }
+                }
+            }
+            if (OP != OP_MTTKRP && BREG) {
+#pragma unroll
+                for (int r = 0; r < BR; ++r) brow[r] = bb[U - 1][r];
+                brow_row = rr[U - 1];
+            }
         }
-        if (OP != OP_LL) flush(cur, cbeg, cend);
+        if (OP != OP_LL) flush(cur, cbeg, cend, brow);
     }
 
     if (OP == OP_LL) {
@@ -382,7 +513,7 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
                     carry_head[c] = v;
                 } else if (complete) {
                     out[(int64_t)crow * Rp + c] = v;
-                    if (OP == OP_PHI) kkt = fmax(kkt, row_violation(__ldg(Bm + (int64_t)crow * Rp + c), v));
+                    if (OP == OP_PHI) kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)crow * Rp + c), v));
                 } else {
                     carry_tail[c] = v;
                 }
@@ -394,7 +525,7 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
             if (__ldg(seg + i) == __ldg(seg + i + 1)) {
                 for (int c = wlane; c < Rp; c += 32) {
                     out[(int64_t)i * Rp + c] = T(0);
-                    if (OP == OP_PHI) kkt = fmax(kkt, row_violation(__ldg(Bm + (int64_t)i * Rp + c), T(0)));
+                    if (OP == OP_PHI) kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)i * Rp + c), T(0)));
                 }
             }
         }
@@ -441,7 +572,7 @@ __global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
         const T v = tot.value();
         reinterpret_cast<T *>(a.out)[(int64_t)row * Rp + c] = v;
         if (OP == OP_PHI)
-            kkt = row_violation(reinterpret_cast<const T *>(a.B)[(int64_t)row * Rp + c], v);
+            kkt = (double)viol_t(reinterpret_cast<const T *>(a.B)[(int64_t)row * Rp + c], v);
     }
     if (OP == OP_PHI && a.inner) publish_kkt<256>(kkt, a.inner, red);
 }
@@ -454,7 +585,7 @@ __global__ void __launch_bounds__(256) kkt_rows_kernel(const T *__restrict__ B, 
     __shared__ double red[8];
     double v = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        v = fmax(v, row_violation(B[e], P[e]));
+        v = fmax(v, (double)viol_t(B[e], P[e]));
     publish_kkt<256>(v, inner, red);
 }
 

@@ -18,8 +18,10 @@ available here, so seeded stand-ins of that shape are drawn instead.
 """
 from __future__ import annotations
 
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 import math
+import os
 
 import numpy as np
 
@@ -69,6 +71,33 @@ def zipf_table(n: int, alpha: float) -> np.ndarray:
     w = np.arange(1, n + 1, dtype=np.float64) ** (-alpha)
     c = np.cumsum(w)
     return c / c[-1]
+
+
+def alias_table(weights: np.ndarray):
+    """Walker's alias table built with Vose's linear algorithm (M. D. Vose,
+    IEEE Trans. Softw. Eng. 17(9), 1991): returns (prob, alias) such that
+    drawing k uniform on [0, n) and keeping k with probability prob[k], else
+    taking alias[k], samples index i with probability weights[i] / sum."""
+    n = weights.size
+    p = (weights / weights.sum() * n).tolist()
+    prob = [1.0] * n
+    alias = list(range(n))
+    small = [i for i in range(n) if p[i] < 1.0]
+    large = [i for i in range(n) if p[i] >= 1.0]
+    while small and large:
+        s = small.pop()
+        g = large.pop()
+        prob[s] = p[s]
+        alias[s] = g
+        p[g] = (p[g] + p[s]) - 1.0
+        (small if p[g] < 1.0 else large).append(g)
+    return np.array(prob), np.array(alias, dtype=np.int64)
+
+
+def _alias_draw(prob: np.ndarray, alias: np.ndarray, u: np.ndarray) -> np.ndarray:
+    x = u * prob.size
+    k = np.minimum(x.astype(np.int64), prob.size - 1)
+    return np.where((x - k) < prob[k], k, alias[k])
 
 
 def poisson_table(mu: float) -> np.ndarray:
@@ -153,15 +182,31 @@ def _draw_mode(spec: TensorSpec, m: int, base: np.uint64, start: int, n: int, ca
     if kind[0] == "uniform":
         return np.minimum((u * dim).astype(np.int64), dim - 1)
     if kind[0] == "zipf":
+        # P(k) proportional to (k + 1)^-alpha, sampled with an alias table
         key = ("zipf", m)
         if key not in cache:
-            table = zipf_table(dim, kind[1])
+            w = np.arange(1, dim + 1, dtype=np.float64) ** (-kind[1])
+            prob, alias = alias_table(w)
             # seeded relabelling so that heavy rows are scattered over the mode
             relabel = np.argsort(uniform01(stream_base(spec.seed, 100 + m), 0, dim), kind="stable")
-            cache[key] = (table, relabel.astype(np.int64))
-        table, relabel = cache[key]
-        return relabel[_inverse_cdf(table, u)]
+            cache[key] = (prob, alias, relabel.astype(np.int64))
+        prob, alias, relabel = cache[key]
+        return relabel[_alias_draw(prob, alias, u)]
     raise ValueError(f"unknown mode distribution {kind}")
+
+
+def _chunked(fn, n: int, chunk: int = 1 << 22) -> None:
+    """Runs fn(lo, hi) over [0, n) in chunks on a thread pool (numpy releases
+    the GIL); the result does not depend on the chunking."""
+    bounds = [(lo, min(lo + chunk, n)) for lo in range(0, n, chunk)]
+    if len(bounds) <= 1:
+        for lo, hi in bounds:
+            fn(lo, hi)
+        return
+    workers = max(1, min(len(bounds), os.cpu_count() or 1, 16))
+    with ThreadPoolExecutor(workers) as ex:
+        for f in [ex.submit(fn, lo, hi) for lo, hi in bounds]:
+            f.result()
 
 
 def generate(spec: TensorSpec) -> SparseTensor:
@@ -179,29 +224,47 @@ def generate(spec: TensorSpec) -> SparseTensor:
         strides[m] = strides[m + 1] * int(spec.dims[m + 1])
     bases = [stream_base(spec.seed, m) for m in range(N)]
     cache: dict = {}
-    parts: list = []
+    # Keep the first spec.nnz distinct coordinates in draw order.  Each round
+    # draws a batch, keeps its first occurrences that are not yet known, and
+    # sizes the next batch from the shortfall.
+    known = np.empty(0, dtype=np.int64)   # sorted distinct keys so far
+    chosen: list = []
+    count = 0
     drawn = 0
     batch = int(spec.nnz * 1.15) + 64
+    for m in range(N):  # build the per-mode tables once, before the threads use them
+        _draw_mode(spec, m, bases[m], 0, 1, cache)
     for _ in range(64):
-        lin = np.zeros(batch, dtype=np.int64)
-        for m in range(N):
-            lin += _draw_mode(spec, m, bases[m], drawn, batch, cache) * strides[m]
+        lin = np.empty(batch, dtype=np.int64)
+
+        def fill(lo, hi, start=drawn, out=lin):
+            acc = np.zeros(hi - lo, dtype=np.int64)
+            for m in range(N):
+                acc += _draw_mode(spec, m, bases[m], start + lo, hi - lo, cache) * strides[m]
+            out[lo:hi] = acc
+
+        _chunked(fill, batch)
         drawn += batch
-        parts.append(lin)
-        allkeys = np.concatenate(parts) if len(parts) > 1 else parts[0]
-        # first occurrence of every distinct coordinate, in draw order
-        order = np.argsort(allkeys, kind="stable")
-        srt = allkeys[order]
+        # first occurrence of each distinct key: smallest draw position per key
+        order = np.argsort(lin)
+        srt = lin[order]
         head = np.ones(srt.size, dtype=bool)
         head[1:] = srt[1:] != srt[:-1]
-        first = np.sort(order[head])
-        if first.size >= spec.nnz:
-            lin = allkeys[first[:spec.nnz]]
+        firstpos = np.minimum.reduceat(order, np.flatnonzero(head))
+        cand = lin[np.sort(firstpos)]
+        if known.size:
+            pos = np.minimum(np.searchsorted(known, cand), known.size - 1)
+            cand = cand[known[pos] != cand]
+        take = cand[:spec.nnz - count]
+        chosen.append(take)
+        count += take.size
+        if count >= spec.nnz:
             break
-        missing = spec.nnz - first.size
-        batch = int(missing * 3) + 1024
+        known = np.sort(np.concatenate([known, cand]), kind="stable")
+        batch = int((spec.nnz - count) * 3) + 1024
     else:
         raise RuntimeError("could not draw enough distinct coordinates")
+    lin = np.concatenate(chosen) if len(chosen) > 1 else chosen[0]
     idx = np.empty((N, lin.size), dtype=np.int64)
     rem = lin.copy()
     for m in range(N):

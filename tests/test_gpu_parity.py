@@ -110,21 +110,25 @@ def test_phi_fp32_matches_oracle(name):
 
 
 @pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)])
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
-def test_phi_rank_lanes(precision, tol, lanes):
-    """Every supported lanes-per-nonzero choice gives the same Phi."""
-    T = case("c3s")
+@pytest.mark.parametrize("rank", [16, 32, 64])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
+def test_phi_rank_lanes(precision, tol, rank, lanes):
+    """Every instantiated lanes-per-nonzero choice gives the same Phi (and MTTKRP)."""
+    T = synth.generate(synth.scaled(synth.C3, 60_000, dims=(8_000, 8_000, 2_000, 365), rank=rank))
     lam, fs = model_for(T, 11)
-    from paper_2307_03276_gb300.cpapr import CpaprError
     try:
         t = cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, rank_lanes=lanes, tile_nnz=1024)
-    except CpaprError:
+    except cpapr.CpaprError as e:
+        assert e.status == 1
         pytest.skip("lanes choice not instantiated for this rank/precision")
     with t:
         t.set_model(lam, fs)
         for n in range(T.nmodes):
             want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
             assert max_rel(t.phi(n), want) <= tol, (lanes, n)
+        assert max_rel(t.mttkrp(2), oracle.mttkrp(T.dims, T.idx, T.vals, fs, 2)) <= tol
+        ll = oracle.loglik(T.dims, T.idx, T.vals, lam, fs)
+        assert abs(t.loglik() - ll) <= (1e-11 if precision == cpapr.CPAPR_FP64 else 1e-5) * abs(ll)
 
 
 @pytest.mark.parametrize("name", ["c1", "c3s", "c5s", "n6"])
