@@ -272,6 +272,57 @@ def timed_solve(cp, torch, T, lam, fs, precision, steps, warmup, dist, use_cuda,
             "mttkrp": mt, "last": r}
 
 
+def batched_run(cp, torch, precision, steps, warmup, count=64):
+    """64 uneven 3-way tensors (dims log-uniform up to 20000 x 20000 x 500, nnz
+    log-uniform 1e3..1e6, R in {8, 16, 32}): one outer iteration per step for
+    the whole batch through the persistent batched solver, and the same work
+    as one cpapr_mu_solve per tensor."""
+    from paper_2307_03276_gb300 import synth
+    specs = synth.batch_specs(count=count)
+    tensors = [synth.generate(s) for s in specs]
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"c4_batch{count}_3way", "tensors": count, "nnz_total": int(sum(T.nnz for T in tensors)),
+           "ranks": sorted({int(T.rank) for T in tensors})}
+    for mode in ("batched", "per_tensor"):
+        ts = [cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, stream=stream.cuda_stream)
+              for T in tensors]
+        for T, t in zip(tensors, ts):
+            t.set_model(np.ones(T.rank), synth.random_factors(T.dims, T.rank, T.seed + 3))
+
+        def step():
+            if mode == "batched":
+                res = cp.cpapr_batch_mu_solve([t.ctx for t in ts], TOL, 1, MAX_INNER)
+            else:
+                res = [t.mu_solve(TOL, 1, MAX_INNER) for t in ts]
+            return sum(r["total_inner"] * T.nnz for r, T in zip(res, tensors))
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        units = 0
+        e0.record(stream)
+        for _ in range(steps):
+            units += step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[mode] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps}
+        for t in ts:
+            t.close()
+    out["speedup_vs_per_tensor"] = out["batched"]["value"] / out["per_tensor"]["value"]
+    return out
+
+
+KERNEL_NAMES = ("phi_tile", "phi_fixup", "mu_update", "normalise", "s_and_b", "loglik", "mttkrp")
+
+
+def kernel_breakdown(stats, steps):
+    """Device milliseconds per step of each kernel kind (library CUDA events)."""
+    return {KERNEL_NAMES[k]: stats[k][1] / steps for k in range(7) if stats[k][0]}
+
+
 def roofline_for(T, inner_per_mode, stats, precision, peaks, cp):
     """Roofline of the Phi tile kernel from its measured average duration."""
     N, nnz, R = T.nmodes, T.nnz, T.rank
@@ -381,7 +432,8 @@ def run_ours(args):
                       "graph": False, "tile_nnz": list(res["info"].tile_nnz)[:T.nmodes],
                       "rank_lanes": list(res["info"].rank_lanes)[:T.nmodes]},
            "roofline": roof, "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
-           "inner_iterations_per_mode": res["inner"].tolist()}
+           "inner_iterations_per_mode": res["inner"].tolist(),
+           "kernel_ms_per_step": kernel_breakdown(res["stats"], args.steps)}
     kern = {}
     mt_l, mt_ms = res["mttkrp"]
     kern["mttkrp_" + args.precision] = {"nnz_per_s": T.nnz * mt_l / (mt_ms / 1e3), "avg_launch_ms": mt_ms / max(mt_l, 1)}
@@ -393,9 +445,16 @@ def run_ours(args):
                                   "dtype": "f32" if other == cp.CPAPR_FP32 else "f64",
                                   "roofline": roofline_for(T, r2["inner"], r2["stats"], other, peaks, cp),
                                   "inner_iterations_per_mode": r2["inner"].tolist(),
+                                  "kernel_ms_per_step": kernel_breakdown(r2["stats"], args.steps),
                                   "loglik_last": r2["last"]["loglik"]}}
         mt_l, mt_ms = r2["mttkrp"]
         kern["mttkrp_" + name] = {"nnz_per_s": T.nnz * mt_l / (mt_ms / 1e3), "avg_launch_ms": mt_ms / max(mt_l, 1)}
+        for pname, prec in (("fp64", cp.CPAPR_FP64), ("fp32", cp.CPAPR_FP32)):
+            b = batched_run(cp, torch, prec, args.steps, args.warmup)
+            ub, sb = aggregate(dist, b["batched"]["value"] * b["batched"]["ms_per_step"] * args.steps / 1e3,
+                               b["batched"]["ms_per_step"] * args.steps / 1e3, use_cuda)
+            b["batched"]["value"] = ub / sb
+            out["variants"]["batched_" + pname] = b
     out["kernels"] = kern
     if not args.no_e2e:
         e2e = e2e_run(cp, torch, T, lam, fs, prim, max(2, args.steps // 2), 1)

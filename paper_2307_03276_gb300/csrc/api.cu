@@ -58,6 +58,23 @@ ProfScope::ProfScope(cpapr_ctx *c, int k) : ctx(c), kind(k) {
     if (!ctx->opt.profile) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (ctx->ev_pool.size() < 2 && !ctx->ev_pending.empty()) {
+        // recycle the pairs that have completed, oldest first, without waiting
+        size_t k = 0;
+        for (; k < ctx->ev_pending.size(); ++k) {
+            auto &p = ctx->ev_pending[k];
+            if (cudaEventQuery(p.second.second) != cudaSuccess) break;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+                ctx->prof_launches[p.first] += 1;
+                ctx->prof_ms[p.first] += ms;
+            }
+            ctx->ev_pool.push_back(p.second.first);
+            ctx->ev_pool.push_back(p.second.second);
+        }
+        cudaGetLastError();
+        ctx->ev_pending.erase(ctx->ev_pending.begin(), ctx->ev_pending.begin() + k);
+    }
     auto take = [&]() {
         cudaEvent_t e = nullptr;
         if (!ctx->ev_pool.empty()) {

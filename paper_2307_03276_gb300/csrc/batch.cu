@@ -1,0 +1,642 @@
+// Batched CP-APR MU: many tensors (uneven nonzero counts and ranks) solved
+// together.  For every mode index n, each step of Algorithm 1 is one launch
+// over all tensors:
+//   batch_sb_kernel      B_t <- (A_t^(n) + S) Lambda_t           (row chunks)
+//   batch_phi_kernel     Phi_t for every tile of every tensor    (persistent,
+//                        blocks pull (tensor, tile) items from a counter;
+//                        each item runs the tile body instantiated for its
+//                        tensor's rank class)
+//   batch_fixup_kernel   rows cut by tile boundaries           (split rows)
+//   batch_update_kernel  B_t <- B_t * Phi_t unless tensor t passed its KKT
+//                        check; per-tensor bookkeeping by the last block of
+//                        the tensor, loop condition by the last block overall
+//   batch_colsum/scale   lambda_t <- e^T B_t, A_t <- B_t Lambda_t^-1
+// The inner loop is one CUDA graph with a conditional WHILE node whose body
+// is {phi, fixup, update}; it runs while any tensor still iterates.  Tensors
+// that converged are masked on the device (their kernels return at once).
+// Every reduction keeps a fixed order (results are reproducible run to run);
+// a tensor's result equals solving it alone up to the order of the column
+// sums (64-row chunks here, row-strided blocks in the single-tensor path).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "phi_kernels.cuh"
+
+namespace cpapr {
+
+cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int reduction);
+cpapr_status launch_loglik_host(cpapr_ctx *ctx, double *host);
+
+namespace {
+
+constexpr int kChunkRows = 64;
+
+struct BatchTensor {
+    PhiArgs a;           // Phi arguments of this tensor for mode n
+    int32_t cfg;         // index into the rank-class case list
+    int32_t rp;
+    int64_t rows;        // I_n
+    void *A;             // A^(n)
+    double *lambda;
+    double *colpart;     // [nchunks][rp] column-sum partials
+    int32_t chunk0, nchunks;
+    double kappa, kappa_tol;
+};
+
+struct BatchCtl {
+    unsigned int tile_next, tile_exit, upd_blocks, active;
+};
+
+// rank classes of the batched Phi kernel: (ranks per lane, lanes), ranks up
+// to 32.  All classes are inlined into one kernel, so its registers are the
+// largest class's: FP32 keeps one float4 per lane; FP64 one lane up to 16
+// ranks and two lanes of 16 ranks for 32.
+template <typename T> struct Classes;
+template <> struct Classes<float> {
+    static constexpr int n = 4;
+    static constexpr int rpl[n] = {4, 4, 4, 4};
+    static constexpr int g[n] = {1, 2, 4, 8};
+};
+template <> struct Classes<double> {
+    static constexpr int n = 5;
+    static constexpr int rpl[n] = {2, 4, 8, 16, 16};
+    static constexpr int g[n] = {1, 1, 1, 1, 2};
+};
+
+template <typename T>
+int class_for(int rp) {
+    for (int k = 0; k < Classes<T>::n; ++k)
+        if (Classes<T>::rpl[k] * Classes<T>::g[k] == rp) return k;
+    return -1;
+}
+
+template <typename T, int RPL, int G>
+__host__ __device__ constexpr int batch_unroll() {
+    return (sizeof(T) == 8 && G == 1) ? 1 : 2;
+}
+
+template <typename T> __host__ __device__ constexpr int batch_threads() { return sizeof(T) == 8 ? 128 : 256; }
+template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 2; }
+
+template <typename T, int NM1, int K>
+__device__ __forceinline__ void run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red) {
+    constexpr int RPL = Classes<T>::rpl[K];
+    constexpr int G = Classes<T>::g[K];
+    phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>()>(a, tile, smem, red);
+}
+
+template <typename T, int NM1>
+__global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) batch_phi_kernel(const BatchTensor *__restrict__ desc,
+                                                                       const int2 *__restrict__ items, int nitems,
+                                                                       BatchCtl *ctl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[batch_threads<T>() / 32];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&ctl->tile_next, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const PhiArgs a = desc[w.x].a;
+        switch (desc[w.x].cfg) {
+            case 0: run_class<T, NM1, 0>(a, w.y, smem_raw, red); break;
+            case 1: run_class<T, NM1, 1>(a, w.y, smem_raw, red); break;
+            case 2: run_class<T, NM1, 2>(a, w.y, smem_raw, red); break;
+            case 3: run_class<T, NM1, 3>(a, w.y, smem_raw, red); break;
+            default:
+                if constexpr (Classes<T>::n > 4) run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0)>(a, w.y, smem_raw, red);
+                break;
+        }
+    }
+    // the last block out resets the work counter for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(&ctl->tile_exit, 1u);
+        if (e == gridDim.x - 1) {
+            ctl->tile_next = 0;
+            ctl->tile_exit = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_fixup_kernel(const BatchTensor *__restrict__ desc,
+                                                          const int2 *__restrict__ items) {
+    __shared__ T sm_s[256];
+    __shared__ T sm_c[256];
+    __shared__ double red[8];
+    const int2 w = items[blockIdx.x];
+    const PhiArgs a = desc[w.x].a;
+    phi_fixup_body<T, OP_PHI>(a, w.y, sm_s, sm_c, red);
+}
+
+// flags[2t] = skip (converged or finished), flags[2t+1] = apply the shift S
+template <typename T>
+__global__ void __launch_bounds__(256) batch_sb_kernel(const BatchTensor *__restrict__ desc,
+                                                       const int2 *__restrict__ chunks, const int32_t *__restrict__ flags) {
+    const int2 w = chunks[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    InnerState *inner = d.a.inner;
+    const bool skip = flags[2 * w.x] != 0;
+    if (w.y == 0 && threadIdx.x == 0) {
+        inner->l = 0;
+        inner->done = skip ? 1 : 0;
+        inner->used = 0;
+        inner->passed = 0;
+        inner->counter = 0;
+        inner->kkt[0] = 0ull;
+        inner->kkt[1] = 0ull;
+        inner->viol = 0.0;
+    }
+    if (skip) return;
+    const int shift = flags[2 * w.x + 1];
+    const int Rp = d.rp;
+    const int64_t r0 = (int64_t)w.y * kChunkRows;
+    const int64_t r1 = min(r0 + kChunkRows, d.rows);
+    const T *A = reinterpret_cast<const T *>(d.A);
+    const T *P = reinterpret_cast<const T *>(d.a.out);
+    T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
+    for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
+        const double a = (double)A[e];
+        const double s = (shift && a < d.kappa_tol && (double)P[e] > 1.0) ? d.kappa : 0.0;
+        B[e] = (T)((a + s) * d.lambda[e % Rp]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__restrict__ desc,
+                                                           const int2 *__restrict__ chunks, unsigned int *chunk_count,
+                                                           BatchCtl *ctl, double tol, int max_inner,
+                                                           cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ int s_l, s_done;
+    __shared__ double s_viol;
+    const int2 w = chunks[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    InnerState *inner = d.a.inner;
+    if (threadIdx.x == 0) {
+        s_l = *((volatile int32_t *)&inner->l);
+        s_done = *((volatile int32_t *)&inner->done);
+        s_viol = __longlong_as_double((long long)inner->kkt[s_l & 1]);
+    }
+    __syncthreads();
+    const int l = s_l, done = s_done;
+    const double viol = s_viol;
+    if (!done && !(viol < tol)) {
+        const int Rp = d.rp;
+        const int64_t r0 = (int64_t)w.y * kChunkRows;
+        const int64_t r1 = min(r0 + kChunkRows, d.rows);
+        T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
+        const T *P = reinterpret_cast<const T *>(d.a.out);
+        for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) B[e] = B[e] * P[e];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&chunk_count[w.x], 1u);
+        if (prev == (unsigned)d.nchunks - 1) {  // last chunk of this tensor: its bookkeeping
+            chunk_count[w.x] = 0;
+            int now_done = done;
+            if (!done) {
+                inner->viol = viol;
+                inner->used = l + 1;
+                if (viol < tol) {
+                    inner->done = 1;
+                    inner->passed = 1;
+                    now_done = 1;
+                }
+            }
+            inner->l = l + 1;
+            inner->kkt[(l + 1) & 1] = 0ull;
+            if (!now_done && l + 1 < max_inner) atomicAdd(&ctl->active, 1u);
+            __threadfence();
+        }
+        const unsigned g = atomicAdd(&ctl->upd_blocks, 1u);
+        if (g == gridDim.x - 1) {  // last block overall: the loop condition
+            __threadfence();
+            const unsigned act = atomicAdd(&ctl->active, 0u);
+            ctl->active = 0;
+            ctl->upd_blocks = 0;
+            __threadfence();
+            if (use_cond) cudaGraphSetConditional(cond, act > 0 ? 1u : 0u);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchTensor *__restrict__ desc,
+                                                           const int2 *__restrict__ chunks,
+                                                           const int32_t *__restrict__ flags) {
+    __shared__ double sm[256];
+    const int2 w = chunks[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    if (flags[2 * w.x]) return;
+    const int Rp = d.rp;
+    const int c = threadIdx.x % Rp, rl = threadIdx.x / Rp, nrl = blockDim.x / Rp;
+    const int64_t r0 = (int64_t)w.y * kChunkRows;
+    const int64_t r1 = min(r0 + kChunkRows, d.rows);
+    const T *B = reinterpret_cast<const T *>(d.a.B);
+    double s = 0.0;
+    if (rl < nrl)
+        for (int64_t i = r0 + rl; i < r1; i += nrl) s += (double)B[i * Rp + c];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < Rp) {
+        double t = 0.0;
+        for (int k = 0; k < nrl; ++k) t += sm[k * Rp + threadIdx.x];
+        d.colpart[(int64_t)w.y * Rp + threadIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_scale_kernel(const BatchTensor *__restrict__ desc,
+                                                          const int2 *__restrict__ chunks,
+                                                          const int32_t *__restrict__ flags) {
+    __shared__ double lam[256];
+    const int2 w = chunks[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    if (flags[2 * w.x]) return;
+    const int Rp = d.rp;
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < d.nchunks; ++p) s += d.colpart[(int64_t)p * Rp + c];
+        lam[c] = s;
+    }
+    __syncthreads();
+    if (w.y == 0)
+        for (int c = threadIdx.x; c < Rp; c += blockDim.x) d.lambda[c] = lam[c];
+    const int64_t r0 = (int64_t)w.y * kChunkRows;
+    const int64_t r1 = min(r0 + kChunkRows, d.rows);
+    const T *B = reinterpret_cast<const T *>(d.a.B);
+    T *A = reinterpret_cast<T *>(d.A);
+    for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
+        const double l = lam[e % Rp];
+        if (l > 0.0) A[e] = (T)((double)B[e] / l);
+    }
+}
+
+__global__ void gather_states_kernel(InnerState *const *src, int n, InnerState *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = *src[i];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct ModePlan {
+    BatchTensor *desc = nullptr;
+    int2 *tiles = nullptr, *splits = nullptr, *chunks = nullptr;
+    int ntiles = 0, nsplits = 0, nchunks = 0;
+    cudaGraphExec_t exec = nullptr;
+    int body_kernels = 0;
+};
+
+struct Plan {
+    std::vector<ModePlan> modes;
+    BatchCtl *ctl = nullptr;
+    unsigned int *chunk_count = nullptr;
+    double *colpart = nullptr;
+    int32_t *flags = nullptr;
+    InnerState **state_ptrs = nullptr;
+    InnerState *states = nullptr;
+    std::vector<void *> owned;
+};
+
+template <typename T>
+cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ctl, cudaStream_t s) {
+    int maxrpl = 0;
+    for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
+    const size_t smem = (size_t)2 * batch_threads<T>() * maxrpl * sizeof(T) + (size_t)2 * batch_threads<T>() * 4;
+    auto go = [&](auto kern) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, batch_threads<T>(), smem, s>>>(mp.desc, mp.tiles, mp.ntiles, ctl);
+        return cudaGetLastError();
+    };
+    switch (nm1) {
+        case 2: return go(batch_phi_kernel<T, 2>);
+        case 3: return go(batch_phi_kernel<T, 3>);
+        case 4: return go(batch_phi_kernel<T, 4>);
+        default: return go(batch_phi_kernel<T, 0>);
+    }
+}
+
+template <typename T>
+int persistent_grid(int nm1) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int maxrpl = 0;
+    for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
+    const size_t smem = (size_t)2 * batch_threads<T>() * maxrpl * sizeof(T) + (size_t)2 * batch_threads<T>() * 4;
+    const void *k = nm1 == 2 ? (const void *)batch_phi_kernel<T, 2>
+                             : nm1 == 3 ? (const void *)batch_phi_kernel<T, 3>
+                                        : nm1 == 4 ? (const void *)batch_phi_kernel<T, 4> : (const void *)batch_phi_kernel<T, 0>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, batch_threads<T>(), smem) != cudaSuccess || per < 1)
+        per = 1;
+    cudaGetLastError();
+    return sms * per;
+}
+
+template <typename T>
+cpapr_status enqueue_inner_body(cpapr_ctx *c0, Plan &P, int n, double tol, int max_inner, cudaGraphConditionalHandle h,
+                                int use_cond, int grid) {
+    ModePlan &mp = P.modes[n];
+    cudaStream_t s = c0->stream;
+    if (mp.ntiles > 0) CPAPR_CUDA(c0, launch_phi_batch<T>(mp, c0->N - 1, grid, P.ctl, s));
+    if (mp.nsplits > 0) {
+        batch_fixup_kernel<T><<<mp.nsplits, 256, 0, s>>>(mp.desc, mp.splits);
+        CPAPR_CUDA(c0, cudaGetLastError());
+    }
+    batch_update_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.chunk_count, P.ctl, tol, max_inner, h,
+                                                      use_cond);
+    CPAPR_CUDA(c0, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+template <typename T>
+cpapr_status build_graph(cpapr_ctx *c0, Plan &P, int n, double tol, int max_inner, int grid) {
+    ModePlan &mp = P.modes[n];
+    cudaGraph_t g = nullptr;
+    CPAPR_CUDA(c0, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c0, e, "cudaGraphConditionalHandleCreate");
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(c0->stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c0, e, "batch graph");
+    }
+    cpapr_status st = enqueue_inner_body<T>(c0, P, n, tol, max_inner, h, 1, grid);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c0->stream, &captured);
+    if (st != CPAPR_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return st != CPAPR_OK ? st : cuda_fail(c0, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&mp.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "cudaGraphInstantiate(batch)");
+    mp.body_kernels = 1 + (mp.nsplits > 0 ? 1 : 0) + 1;
+    return CPAPR_OK;
+}
+
+void free_plan(Plan &P) {
+    for (auto &mp : P.modes)
+        if (mp.exec) cudaGraphExecDestroy(mp.exec);
+    for (void *p : P.owned) cudaFree(p);
+    P.owned.clear();
+}
+
+template <typename T>
+cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
+                           cpapr_result *results) {
+    cpapr_ctx *c0 = ctxs[0];
+    const int N = c0->N;
+    cudaStream_t s = c0->stream;
+    for (int i = 0; i < count; ++i) CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+    // every tensor needs a rank class of the batched kernel and the segmented reduction
+    for (int i = 0; i < count; ++i) {
+        const int k = class_for<T>(ctxs[i]->Rp);
+        if (k < 0) return fail(ctxs[i], CPAPR_E_ARG, "rank not supported by the batched solver");
+        const int lanes = (sizeof(T) == 8 ? Classes<T>::g[k] : Classes<T>::g[k]);
+        for (int n = 0; n < N; ++n) {
+            ModeLayout &L = ctxs[i]->mode[n];
+            if (L.lanes != lanes || L.reduction != CPAPR_REDUCE_SEGMENTED)
+                CPAPR_TRY(configure_mode(ctxs[i], n, lanes, L.tile_nnz, CPAPR_REDUCE_SEGMENTED));
+        }
+        CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+    }
+    Plan P;
+    P.modes.resize(N);
+    auto dalloc = [&](void **p, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) P.owned.push_back(*p);
+        return e;
+    };
+#define BT_CUDA(call)                               \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) {                    \
+            free_plan(P);                           \
+            return cuda_fail(c0, _e, #call);        \
+        }                                           \
+    } while (0)
+    // per-tensor column partial areas (sized for the longest mode)
+    std::vector<int64_t> colpart_off(count);
+    int64_t colpart_total = 0;
+    for (int i = 0; i < count; ++i) {
+        int64_t mx = 0;
+        for (int n = 0; n < N; ++n) mx = std::max<int64_t>(mx, ceil_div(ctxs[i]->dims[n], kChunkRows));
+        colpart_off[i] = colpart_total;
+        colpart_total += mx * ctxs[i]->Rp;
+    }
+    BT_CUDA(dalloc((void **)&P.colpart, (size_t)colpart_total * 8));
+    BT_CUDA(dalloc((void **)&P.ctl, sizeof(BatchCtl)));
+    BT_CUDA(dalloc((void **)&P.chunk_count, (size_t)count * 4));
+    BT_CUDA(dalloc((void **)&P.flags, (size_t)count * 8));
+    BT_CUDA(dalloc((void **)&P.state_ptrs, (size_t)count * N * sizeof(InnerState *)));
+    BT_CUDA(dalloc((void **)&P.states, (size_t)count * N * sizeof(InnerState)));
+    BT_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(BatchCtl), s));
+    BT_CUDA(cudaMemsetAsync(P.chunk_count, 0, (size_t)count * 4, s));
+    {
+        std::vector<InnerState *> sp((size_t)count * N);
+        for (int i = 0; i < count; ++i)
+            for (int n = 0; n < N; ++n) sp[(size_t)i * N + n] = ctxs[i]->inner + n;
+        BT_CUDA(cudaMemcpy(P.state_ptrs, sp.data(), sp.size() * sizeof(InnerState *), cudaMemcpyHostToDevice));
+    }
+    for (int n = 0; n < N; ++n) {
+        ModePlan &mp = P.modes[n];
+        std::vector<BatchTensor> desc(count);
+        std::vector<int2> tiles, chunks;
+        std::vector<int2> splits;
+        for (int i = 0; i < count; ++i) {
+            cpapr_ctx *c = ctxs[i];
+            const ModeLayout &L = c->mode[n];
+            BatchTensor &d = desc[i];
+            std::memset(&d, 0, sizeof(d));
+            PhiArgs &a = d.a;
+            a.nnz = c->nnz;
+            a.T = L.tile_nnz;
+            a.ntiles = L.ntiles;
+            a.Rp = c->Rp;
+            a.In = L.In;
+            a.nm1 = c->N - 1;
+            a.atomic = 0;
+            a.seg = L.seg;
+            int k = 0;
+            for (int m = 0; m < N; ++m) {
+                if (m == n) continue;
+                a.idx[k] = L.idx[k];
+                a.A[k] = c->A[m];
+                ++k;
+            }
+            a.val = L.val;
+            a.B = c->B;
+            a.out = c->Phi[n];
+            a.carry = c->carry;
+            a.row_first = L.row_first;
+            a.row_lo = L.row_lo;
+            a.split = L.split;
+            a.nsplit = L.nsplit;
+            a.eps = c->opt.eps;
+            a.inner = c->inner + n;
+            a.llpart = c->llpart;
+            d.cfg = class_for<T>(c->Rp);
+            d.rp = c->Rp;
+            d.rows = c->dims[n];
+            d.A = c->A[n];
+            d.lambda = c->lambda;
+            d.colpart = P.colpart + colpart_off[i];
+            d.nchunks = (int32_t)ceil_div(c->dims[n], kChunkRows);
+            d.chunk0 = (int32_t)chunks.size();
+            d.kappa = c->opt.kappa;
+            d.kappa_tol = c->opt.kappa_tol;
+            for (int t = 0; t < (c->nnz > 0 ? L.ntiles : 0); ++t) tiles.push_back(make_int2(i, t));
+            for (int t = 0; t < (c->nnz > 0 ? L.nsplit : 0); ++t) splits.push_back(make_int2(i, t));
+            for (int t = 0; t < d.nchunks; ++t) chunks.push_back(make_int2(i, t));
+        }
+        // larger tensors' tiles first: the persistent blocks finish together
+        std::stable_sort(tiles.begin(), tiles.end(), [&](const int2 &x, const int2 &y) {
+            return ctxs[x.x]->nnz > ctxs[y.x]->nnz;
+        });
+        mp.ntiles = (int)tiles.size();
+        mp.nsplits = (int)splits.size();
+        mp.nchunks = (int)chunks.size();
+        BT_CUDA(dalloc((void **)&mp.desc, desc.size() * sizeof(BatchTensor)));
+        BT_CUDA(dalloc((void **)&mp.tiles, tiles.size() * sizeof(int2)));
+        BT_CUDA(dalloc((void **)&mp.splits, splits.size() * sizeof(int2)));
+        BT_CUDA(dalloc((void **)&mp.chunks, chunks.size() * sizeof(int2)));
+        BT_CUDA(cudaMemcpy(mp.desc, desc.data(), desc.size() * sizeof(BatchTensor), cudaMemcpyHostToDevice));
+        if (!tiles.empty())
+            BT_CUDA(cudaMemcpy(mp.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        if (!splits.empty())
+            BT_CUDA(cudaMemcpy(mp.splits, splits.data(), splits.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        BT_CUDA(cudaMemcpy(mp.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+    const int grid = persistent_grid<T>(N - 1);
+    const bool graph = c0->opt.use_graph != 0;
+    if (graph)
+        for (int n = 0; n < N; ++n) {
+            cpapr_status st = build_graph<T>(c0, P, n, tol, max_inner, grid);
+            if (st != CPAPR_OK) {
+                free_plan(P);
+                return st;
+            }
+        }
+
+    struct Track {
+        int outer = 0, total = 0;
+        bool conv = false, active = true;
+        double kkt = 0.0;
+    };
+    std::vector<Track> tr(count);
+    std::vector<int32_t> flags((size_t)count * 2);
+    std::vector<InnerState> hs((size_t)count * N);
+    cpapr_status st = CPAPR_OK;
+    for (int k = 0; k < max_outer && st == CPAPR_OK; ++k) {
+        bool any = false;
+        for (int i = 0; i < count; ++i) {
+            flags[2 * i] = tr[i].active ? 0 : 1;
+            flags[2 * i + 1] = ctxs[i]->k_total > 0 ? 1 : 0;
+            any = any || tr[i].active;
+        }
+        if (!any) break;
+        BT_CUDA(cudaMemcpyAsync(P.flags, flags.data(), flags.size() * 4, cudaMemcpyHostToDevice, s));
+        for (int n = 0; n < N; ++n) {
+            ModePlan &mp = P.modes[n];
+            batch_sb_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
+            BT_CUDA(cudaGetLastError());
+            if (graph) {
+                BT_CUDA(cudaGraphLaunch(mp.exec, s));
+            } else {
+                for (int l = 0; l < max_inner && st == CPAPR_OK; ++l)
+                    st = enqueue_inner_body<T>(c0, P, n, tol, max_inner, 0ull, 0, grid);
+                if (st != CPAPR_OK) break;
+            }
+            batch_colsum_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
+            batch_scale_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
+            BT_CUDA(cudaGetLastError());
+        }
+        if (st != CPAPR_OK) break;
+        gather_states_kernel<<<(unsigned)ceil_div((int64_t)count * N, 256), 256, 0, s>>>(P.state_ptrs, count * N,
+                                                                                      P.states);
+        BT_CUDA(cudaGetLastError());
+        BT_CUDA(cudaMemcpyAsync(hs.data(), P.states, hs.size() * sizeof(InnerState), cudaMemcpyDeviceToHost, s));
+        BT_CUDA(cudaStreamSynchronize(s));
+        c0->launches += 1 + (int64_t)N * 3;
+        for (int i = 0; i < count; ++i) {
+            if (!tr[i].active) continue;
+            cpapr_ctx *c = ctxs[i];
+            c->k_total += 1;
+            tr[i].outer += 1;
+            bool all_first = true;
+            double kmax = 0.0;
+            for (int n = 0; n < N; ++n) {
+                const InnerState &x = hs[(size_t)i * N + n];
+                tr[i].total += x.used;
+                if (!(x.passed && x.used == 1)) all_first = false;
+                kmax = std::max(kmax, x.viol);
+            }
+            tr[i].kkt = kmax;
+            if (all_first) {
+                tr[i].conv = true;
+                tr[i].active = false;
+            }
+        }
+        int used_max = 0;
+        for (int n = 0; n < N; ++n) {
+            int um = 0;
+            for (int i = 0; i < count; ++i) um = std::max(um, hs[(size_t)i * N + n].used);
+            used_max += um * P.modes[n].body_kernels;
+        }
+        c0->launches += used_max;
+    }
+    free_plan(P);
+#undef BT_CUDA
+    if (st != CPAPR_OK) return st;
+    for (int i = 0; i < count; ++i) {
+        double ll = 0.0;
+        CPAPR_TRY(launch_loglik_host(ctxs[i], &ll));
+        results[i].outer_iters = tr[i].outer;
+        results[i].total_inner = tr[i].total;
+        results[i].converged = tr[i].conv ? 1 : 0;
+        results[i].reserved = 0;
+        results[i].loglik = ll;
+        results[i].kkt_viol = tr[i].kkt;
+    }
+    return CPAPR_OK;
+}
+
+}  // namespace
+
+// Batched solve through the persistent kernels; contexts must share the
+// device, the precision and the number of modes.
+cpapr_status batch_mu_solve_persistent(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
+                                       cpapr_result *results) {
+    if (count == 0) return CPAPR_OK;
+    for (int i = 1; i < count; ++i)
+        if (ctxs[i]->N != ctxs[0]->N || ctxs[i]->device != ctxs[0]->device)
+            return fail(ctxs[i], CPAPR_E_ARG, "batched solve needs one device and one number of modes");
+    if (ctxs[0]->esize == 8) return batch_solve_t<double>(ctxs, count, tol, max_outer, max_inner, results);
+    return batch_solve_t<float>(ctxs, count, tol, max_outer, max_inner, results);
+}
+
+}  // namespace cpapr

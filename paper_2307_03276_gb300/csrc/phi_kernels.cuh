@@ -273,8 +273,17 @@ __device__ __forceinline__ void store_row(T *__restrict__ base, const T (&src)[R
 
 // NM1: number of gathered modes (exact), or 0 for "runtime count up to kMaxNm1".
 // U: nonzeros whose gathers are issued together (memory-level parallelism).
+// Shared memory of one block: partial-row slots, 2 per group.
+template <typename T, int RPL, int THREADS>
+constexpr size_t phi_slot_bytes() {
+    return (size_t)2 * THREADS * RPL * sizeof(T) + (size_t)2 * THREADS * 4;
+}
+
+// One tile (t) of one tensor (a) by the whole block.  Every thread of the
+// block must call it with the same arguments.  smem_raw holds the slots
+// (phi_slot_bytes), red is NWARPS doubles.
 template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
-__global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
+__device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red) {
     constexpr int NG = THREADS / G;
     constexpr int NWARPS = THREADS / 32;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
@@ -283,7 +292,6 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     const int tid = threadIdx.x;
     const int g = tid / G, lane = tid % G;
     const int warp = tid >> 5, wlane = tid & 31;
-    const int t = blockIdx.x;
     const int Rp = RPL * G;
     const int64_t p0 = (int64_t)t * a.T;
     const int64_t p1 = min(p0 + (int64_t)a.T, a.nnz);
@@ -293,13 +301,12 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     const int col0 = lane * RPL;
     const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((wlane / G) * G));
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *slot_val = reinterpret_cast<T *>(smem_raw);                  // [2 * NG][Rp]
     int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
-    __shared__ double red[NWARPS];
 
     const bool segmented = (OP != OP_LL) && !a.atomic;
     if (segmented) {
+        __syncthreads();  // the previous tile of a persistent block may still read the slots
         for (int s = tid; s < 2 * NG; s += THREADS) slot_row[s] = -1;
         __syncthreads();
     }
@@ -533,18 +540,24 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     if (OP == OP_PHI && a.inner && !a.atomic) publish_kkt<THREADS>(kkt, a.inner, red);
 }
 
+// One block per tile of one tensor.
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+__global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[THREADS / 32];
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red);
+}
+
 // Adds the per-tile partials of every row that spans tiles, in tile order,
 // and stores the row (plus its KKT violation).  One block per such row.
+// Body for split row `si` of tensor `a`; 256 threads, all calling it.
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
+__device__ __forceinline__ void phi_fixup_body(const PhiArgs &a, const int si, T *sm_s, T *sm_c, double *red) {
     if (a.inner && a.inner->done) return;
-    __shared__ T sm_s[256];
-    __shared__ T sm_c[256];
-    __shared__ double red[8];
     const int Rp = a.Rp;
-    const int32_t row = a.split[3 * blockIdx.x + 0];
-    const int32_t t0 = a.split[3 * blockIdx.x + 1];
-    const int32_t t1 = a.split[3 * blockIdx.x + 2];
+    const int32_t row = a.split[3 * si + 0];
+    const int32_t t0 = a.split[3 * si + 1];
+    const int32_t t1 = a.split[3 * si + 2];
     const int c = threadIdx.x % Rp;
     const int chunk = threadIdx.x / Rp;
     const int nchunks = blockDim.x / Rp;
@@ -575,6 +588,15 @@ __global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
             kkt = (double)viol_t(reinterpret_cast<const T *>(a.B)[(int64_t)row * Rp + c], v);
     }
     if (OP == OP_PHI && a.inner) publish_kkt<256>(kkt, a.inner, red);
+    __syncthreads();  // sm_s / sm_c are reused by the next split row of a persistent block
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
+    __shared__ T sm_s[256];
+    __shared__ T sm_c[256];
+    __shared__ double red[8];
+    phi_fixup_body<T, OP>(a, blockIdx.x, sm_s, sm_c, red);
 }
 
 // KKT violation over all rows (used after the atomic reduction).

@@ -107,6 +107,11 @@ static cpapr_status loglik_now(cpapr_ctx *ctx, double *host) {
     return CPAPR_OK;
 }
 
+cpapr_status launch_loglik_host(cpapr_ctx *ctx, double *host) { return loglik_now(ctx, host); }
+
+cpapr_status batch_mu_solve_persistent(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
+                                       cpapr_result *results);
+
 cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, cpapr_result *res,
                       int32_t *inner_trace, double *ll_trace) {
     const int N = ctx->N;
@@ -149,12 +154,18 @@ cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, 
     return CPAPR_OK;
 }
 
-// Batch: the contexts' outer iterations advance in lock step; the work of
-// all still-running contexts is enqueued on their streams before any host
-// synchronisation, so one round trip per outer iteration covers the batch.
+// Batch.  Contexts that share the device and the number of modes run through
+// the persistent batched kernels (batch.cu).  Otherwise the contexts' outer
+// iterations advance in lock step: the work of all still-running contexts is
+// enqueued on their streams before any host synchronisation, so one round
+// trip per outer iteration covers the batch.
 cpapr_status batch_mu_solve(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
                             cpapr_result *results) {
     if (count == 0) return CPAPR_OK;
+    bool uniform = true;
+    for (int i = 1; i < count; ++i)
+        uniform = uniform && ctxs[i]->N == ctxs[0]->N && ctxs[i]->device == ctxs[0]->device;
+    if (uniform) return batch_mu_solve_persistent(ctxs, count, tol, max_outer, max_inner, results);
     struct Track {
         int outer = 0, total = 0;
         bool conv = false, active = true;

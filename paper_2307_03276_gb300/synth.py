@@ -303,14 +303,16 @@ def random_tensor(dims, nnz: int, rank: int, seed: int, values=("poisson1", 1.0)
 
 def batch_specs(count: int = 64, seed: int = 1004, nnz_range=(1e3, 1e6),
                 dim_lo=(50, 50, 50), dim_hi=(20_000, 20_000, 500), ranks=(8, 16, 32)) -> list:
-    """Per-tensor specs: log-uniform dims and nnz, Zipf(1.2) modes, Poisson(1)+1 counts."""
+    """Per-tensor specs: log-uniform dims and nnz, Zipf(1.2) modes, Poisson(1)+1 counts.
+    nnz is capped at 10% of the coordinate space: Zipf-distributed coordinates
+    cannot practically fill a larger share of a small space."""
     b = stream_base(seed, 0)
     specs = []
     for t in range(count):
         u = uniform01(b, 8 * t, 8)
         dims = tuple(int(round(math.exp(math.log(lo) + u[m] * (math.log(hi) - math.log(lo)))))
                      for m, (lo, hi) in enumerate(zip(dim_lo, dim_hi)))
-        cap = 0.5 * dims[0] * dims[1] * dims[2]
+        cap = 0.1 * dims[0] * dims[1] * dims[2]
         nnz = int(round(math.exp(math.log(nnz_range[0]) + u[3] * (math.log(nnz_range[1]) - math.log(nnz_range[0])))))
         nnz = int(min(nnz, cap))
         rank = ranks[min(int(u[4] * len(ranks)), len(ranks) - 1)]

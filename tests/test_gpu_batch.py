@@ -1,0 +1,99 @@
+"""Batched CP-APR MU (cpapr_batch_mu_solve): many uneven tensors in one
+persistent launch per step, against solving each tensor alone and against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_03276_gb300 import cpapr, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2307_03276_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def batch_tensors(count=7, seed=77):
+    specs = synth.batch_specs(count=count, seed=seed, nnz_range=(300, 30_000), dim_hi=(2_000, 2_000, 200))
+    out = []
+    for k, sp in enumerate(specs):
+        if k == 0:  # a rank-1 tensor converges after two outer iterations and gets masked
+            sp = synth.TensorSpec(sp.dims, sp.nnz, 1, sp.modes, sp.values, sp.seed, sp.name)
+        T = synth.generate(sp)
+        out.append(T)
+    return out
+
+
+def models(tensors):
+    res = []
+    for T in tensors:
+        fs = synth.random_factors(T.dims, T.rank, T.seed + 3)
+        res.append((np.ones(T.rank), fs))
+    return res
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_batch_fp64_equals_individual_solves_and_oracle(use_graph):
+    Ts = batch_tensors()
+    ms = models(Ts)
+    tol, mo, mi = 1e-4, 6, 5
+    batch = [cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, use_graph=use_graph) for T in Ts]
+    for t, (lam, fs) in zip(batch, ms):
+        t.set_model(lam, fs)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in batch], tol, mo, mi)
+    for T, t, (lam, fs), r in zip(Ts, batch, ms, res):
+        lb, fb = t.get_model()
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as s:
+            s.set_model(lam, fs)
+            ri = s.mu_solve(tol, mo, mi)
+            li, fi = s.get_model()
+        assert (r["outer_iters"], r["total_inner"], r["converged"]) == (ri["outer_iters"], ri["total_inner"],
+                                                                          ri["converged"])
+        # same kernels and tiles; only the column sums are added in another fixed order
+        np.testing.assert_allclose(lb, li, rtol=1e-12)
+        for a, b in zip(fb, fi):
+            np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-15 * b.max())
+        ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=tol, max_outer=mo, max_inner=mi)
+        assert r["outer_iters"] == ref["outer_iters"] and r["total_inner"] == ref["total_inner"]
+        np.testing.assert_allclose(lb, ref["lambda"], rtol=1e-10)
+        for a, b in zip(fb, ref["factors"]):
+            np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-14 * b.max())
+        assert abs(r["loglik"] - ref["loglik"][-1]) <= 1e-11 * abs(ref["loglik"][-1])
+        t.close()
+    assert res[0]["converged"] and res[0]["outer_iters"] == 2
+
+
+def test_batch_fp32_close_to_individual():
+    Ts = batch_tensors(seed=78)
+    ms = models(Ts)
+    batch = [cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=cpapr.CPAPR_FP32) for T in Ts]
+    for t, (lam, fs) in zip(batch, ms):
+        t.set_model(lam, fs)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in batch], 1e-4, 3, 5)
+    for T, t, (lam, fs), r in zip(Ts, batch, ms, res):
+        lb, fb = t.get_model()
+        ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=3, max_inner=5)
+        np.testing.assert_allclose(lb, ref["lambda"], rtol=1e-4)
+        assert abs(r["loglik"] - ref["loglik"][-1]) <= 1e-5 * abs(ref["loglik"][-1])
+        t.close()
+
+
+def test_batch_mixed_modes_falls_back():
+    """Tensors with different numbers of modes still solve (lock-step path)."""
+    a = synth.random_tensor((30, 20, 10), 800, 4, 5)
+    b = synth.random_tensor((12, 10, 8, 6), 900, 4, 6)
+    ts = []
+    for T in (a, b):
+        t = cpapr.Tensor(T.dims, T.idx, T.vals, T.rank)
+        t.set_model(np.ones(4), synth.random_factors(T.dims, 4, 9))
+        ts.append(t)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in ts], 1e-4, 2, 3)
+    for T, t, r in zip((a, b), ts, res):
+        ref = oracle.mu_solve(T.dims, T.idx, T.vals, np.ones(4), synth.random_factors(T.dims, 4, 9), tol=1e-4,
+                              max_outer=2, max_inner=3)
+        np.testing.assert_allclose(t.get_model()[0], ref["lambda"], rtol=1e-10)
+        t.close()
