@@ -141,6 +141,21 @@ cpapr_status cpapr_init_random(cpapr_ctx *ctx, uint64_t seed);
 cpapr_status cpapr_get_model(cpapr_ctx *ctx, double *lambda, double *const *factors);
 
 /*
+ * Checkpoint / resume.  The state the MU loop of Algorithm 1 carries from one
+ * outer iteration to the next: the model (lambda, factors), the Phi^(m) of
+ * each mode's last inner iteration (I_m x R doubles each; the shift S of the
+ * next iteration reads it) and the number of outer iterations run since the
+ * model was set.  Restoring a state into a context built from the same
+ * tensor with the same options continues the solve exactly as if it had not
+ * stopped (bit for bit).  phi_prev may be NULL in cpapr_get_state to skip it;
+ * in cpapr_set_state NULL means zeros (no shift).
+ */
+cpapr_status cpapr_get_state(cpapr_ctx *ctx, double *lambda, double *const *factors, double *const *phi_prev,
+                             int64_t *outer_done);
+cpapr_status cpapr_set_state(cpapr_ctx *ctx, const double *lambda, const double *const *factors,
+                             const double *const *phi_prev, int64_t outer_done);
+
+/*
  * Phi^(mode) of Algorithm 2 for the current factors.  B is I_mode x R; pass
  * NULL to use B = A^(mode) diag(lambda) (Algorithm 1 without S).  out
  * receives I_mode x R doubles.  Errors: E_ARG, E_STATE (no model), E_CUDA.

@@ -83,6 +83,8 @@ def load() -> ctypes.CDLL:
     lib.cpapr_get_model.argtypes = [P, P, P]
     lib.cpapr_phi.argtypes = [P, i32, P, P]
     lib.cpapr_phi_noalloc.argtypes = [P, i32, P, P]
+    lib.cpapr_get_state.argtypes = [P, P, P, P, ctypes.POINTER(i64)]
+    lib.cpapr_set_state.argtypes = [P, P, P, P, i64]
     lib.cpapr_mttkrp.argtypes = [P, i32, P]
     lib.cpapr_loglik.argtypes = [P, P]
     lib.cpapr_mu_solve.argtypes = [P, f64, i32, i32, ctypes.POINTER(Result), P, P]
@@ -94,7 +96,7 @@ def load() -> ctypes.CDLL:
     lib.cpapr_version.argtypes = []
     lib.cpapr_version.restype = ctypes.c_char_p
     for name in ("cpapr_create", "cpapr_set_model", "cpapr_init_random", "cpapr_get_model", "cpapr_phi",
-                 "cpapr_phi_noalloc",
+                 "cpapr_phi_noalloc", "cpapr_get_state", "cpapr_set_state",
                  "cpapr_mttkrp", "cpapr_loglik", "cpapr_mu_solve", "cpapr_batch_mu_solve", "cpapr_get_info",
                  "cpapr_kernel_stats"):
         getattr(lib, name).restype = ctypes.c_int
@@ -197,6 +199,32 @@ def cpapr_get_model(ctx):
     arr = (ctypes.c_void_p * len(fs))(*[A.ctypes.data for A in fs])
     _check(load().cpapr_get_model(ctx, lam.ctypes.data, arr), ctx)
     return lam, fs
+
+
+def cpapr_get_state(ctx) -> dict:
+    """Checkpoint: lambda, factors, each mode's last Phi and the outer-iteration count."""
+    info = cpapr_get_info(ctx)
+    R = info.rank
+    lam = np.zeros(R)
+    fs = [np.zeros((info.dims[m], R)) for m in range(info.nmodes)]
+    ph = [np.zeros((info.dims[m], R)) for m in range(info.nmodes)]
+    arr_f = (ctypes.c_void_p * len(fs))(*[A.ctypes.data for A in fs])
+    arr_p = (ctypes.c_void_p * len(ph))(*[A.ctypes.data for A in ph])
+    k = ctypes.c_int64()
+    _check(load().cpapr_get_state(ctx, lam.ctypes.data, arr_f, arr_p, ctypes.byref(k)), ctx)
+    return {"lambda": lam, "factors": fs, "phi_prev": ph, "outer_done": k.value}
+
+
+def cpapr_set_state(ctx, state: dict) -> None:
+    lam = _as_f64(state["lambda"])
+    fs = [_as_f64(A) for A in state["factors"]]
+    arr_f = (ctypes.c_void_p * len(fs))(*[_ptr(A) for A in fs])
+    ph = state.get("phi_prev")
+    arr_p = None
+    if ph is not None:
+        ph = [_as_f64(A) for A in ph]
+        arr_p = (ctypes.c_void_p * len(ph))(*[_ptr(A) for A in ph])
+    _check(load().cpapr_set_state(ctx, _ptr(lam), arr_f, arr_p, int(state.get("outer_done", 0))), ctx)
 
 
 def _out_matrix(ctx, mode, out):

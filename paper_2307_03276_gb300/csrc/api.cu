@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -36,8 +38,29 @@ cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, CPAPR_E_CUDA, msg);
 }
 
+// Host-side fault injection for testing error paths: when the environment
+// variable CPAPR_FAULT_ALLOC_AT holds k > 0, the k-th context allocation
+// counted from the moment that value was first seen reports CPAPR_E_NOMEM
+// (no device call fails; nothing is done to the GPU).
+static bool injected_alloc_failure() {
+    static std::mutex mu;
+    static std::string seen;
+    static long long calls = 0;
+    const char *s = std::getenv("CPAPR_FAULT_ALLOC_AT");
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string v = s ? s : "";
+    if (v != seen) {
+        seen = v;
+        calls = 0;
+    }
+    if (v.empty()) return false;
+    const long long k = std::atoll(v.c_str());
+    return k > 0 && ++calls == k;
+}
+
 cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
+    if (injected_alloc_failure()) return fail(ctx, CPAPR_E_NOMEM, "injected allocation failure (CPAPR_FAULT_ALLOC_AT)");
     cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
     ctx->allocs.push_back(*p);
@@ -121,19 +144,23 @@ static int next_pow2(int v) {
 }
 
 // Built-in choice of lanes per nonzero and nonzeros per tile (from sweeps on
-// GB300).  FP64: one lane per nonzero up to 16 ranks (no shuffle adds on the
-// scarce FP64 pipe), 16 ranks per lane above with batches of two nonzeros, so
-// that every nonzero still costs one division; FP32: 16-byte vectors of 4
-// ranks per lane up to 32 ranks, 8 ranks per lane above.
+// GB300 over the 1e7-nonzero 3-way and 5e7-nonzero 4-way workloads).  FP64:
+// one lane per nonzero up to 16 ranks (no shuffle adds on the scarce FP64
+// pipe), 8 ranks per lane above with batches of two nonzeros; FP32: 16-byte
+// vectors of 4 ranks per lane up to 32 ranks, 8 ranks per lane above, and
+// larger tiles for large tensors (fewer rows cut across tiles).
 static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
     const int Rp = ctx->Rp;
     int g;
     if (ctx->esize == 8)
-        g = Rp <= 16 ? 1 : Rp / 16;
+        g = Rp <= 16 ? 1 : Rp / 8;
     else
         g = Rp <= 32 ? std::max(1, Rp / 4) : Rp / 8;
     *lanes = g;
-    *tile = ctx->esize == 8 ? 2048 : 4096;
+    if (ctx->esize == 8)
+        *tile = Rp <= 16 ? 2048 : 1024;
+    else
+        *tile = ctx->nnz >= 30000000 ? 8192 : 4096;
     *reduction = CPAPR_REDUCE_SEGMENTED;
     (void)n;
 }
@@ -377,6 +404,41 @@ cpapr_status cpapr_get_model(cpapr_ctx *ctx, double *lambda, double *const *fact
             CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         }
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_get_state(cpapr_ctx *ctx, double *lambda, double *const *factors, double *const *phi_prev,
+                             int64_t *outer_done) {
+    API_ENTER(ctx);
+    CPAPR_TRY(cpapr_get_model(ctx, lambda, factors));
+    if (phi_prev)
+        for (int m = 0; m < ctx->N; ++m) {
+            if (!phi_prev[m]) continue;
+            CPAPR_TRY(download_matrix(ctx, ctx->Phi[m], ctx->dims[m], phi_prev[m]));
+            CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+    if (outer_done) *outer_done = ctx->k_total;
+    return CPAPR_OK;
+}
+
+cpapr_status cpapr_set_state(cpapr_ctx *ctx, const double *lambda, const double *const *factors,
+                             const double *const *phi_prev, int64_t outer_done) {
+    API_ENTER(ctx);
+    if (outer_done < 0) return fail(ctx, CPAPR_E_ARG, "outer_done must be >= 0");
+    CPAPR_TRY(cpapr_set_model(ctx, lambda, factors));
+    if (phi_prev) {
+        CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, 16, ctx->stream));
+        for (int m = 0; m < ctx->N; ++m)
+            if (phi_prev[m]) CPAPR_TRY(upload_matrix(ctx, phi_prev[m], ctx->dims[m], ctx->Phi[m]));
+        int32_t flags[4] = {0, 0, 0, 0};
+        CPAPR_CUDA(ctx, cudaMemcpyAsync(flags, ctx->errflag, 16, cudaMemcpyDeviceToHost, ctx->stream));
+        CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flags[2]) {
+            ctx->model_set = false;
+            return fail(ctx, CPAPR_E_VALUE, "phi_prev entries must be finite and >= 0");
+        }
+    }
+    ctx->k_total = outer_done;
     return CPAPR_OK;
 }
 

@@ -21,8 +21,8 @@ bool phi_config_supported(int esize, int nm1, int rp, int lanes) {
     if (lanes < 1 || rp % lanes) return false;
     const int rpl = rp / lanes;
     if (esize == 8) {
-        static const int ok[][2] = {{2, 1}, {4, 1},  {8, 1},  {16, 1}, {32, 1}, {8, 2},
-                                    {16, 2}, {32, 2}, {8, 4}, {16, 4}, {32, 4}, {16, 8}};
+        static const int ok[][2] = {{2, 1}, {4, 1},  {8, 1}, {16, 1}, {8, 2},  {16, 2},
+                                    {8, 4}, {16, 4}, {8, 8}, {16, 8}, {8, 16}};
         for (auto &p : ok)
             if (p[0] == rpl && p[1] == lanes) return true;
     } else {

@@ -54,14 +54,13 @@ cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s)
     CPAPR_CASE(4, 1)
     CPAPR_CASE(8, 1)
     CPAPR_CASE(16, 1)
-    CPAPR_CASE(32, 1)
     CPAPR_CASE(8, 2)
     CPAPR_CASE(16, 2)
-    CPAPR_CASE(32, 2)
     CPAPR_CASE(8, 4)
     CPAPR_CASE(16, 4)
-    CPAPR_CASE(32, 4)
+    CPAPR_CASE(8, 8)
     CPAPR_CASE(16, 8)
+    CPAPR_CASE(8, 16)
 #else
     CPAPR_CASE(4, 1)
     CPAPR_CASE(8, 1)

@@ -232,12 +232,13 @@ __device__ __forceinline__ T dot_global(const T *__restrict__ base, const T (&v)
     return d;
 }
 
-// <a, b>.  FP32: four independent partial sums (short dependency chains);
-// FP64: one chain, because on this GPU the FP64 pipe itself is the limit
-// and every extra add costs a pipe slot.
+// <a, b>.  FP32 with 8 or more ranks per lane: four independent partial sums
+// (short dependency chains); otherwise one FMA chain -- for FP64 because on
+// this GPU the FP64 pipe itself is the limit and every extra add costs a
+// pipe slot.
 template <typename T, int RPL>
 __device__ __forceinline__ T dot_regs(const T (&a)[RPL], const T (&b)[RPL]) {
-    if constexpr (RPL < 4 || sizeof(T) == 8) {
+    if constexpr (RPL < 8 || sizeof(T) == 8) {
         T d = T(0);
 #pragma unroll
         for (int r = 0; r < RPL; ++r) d = fma(a[r], b[r], d);
@@ -335,9 +336,15 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
         int64_t rbeg = __ldg(seg + row);
         int32_t cur = row;
         int64_t cbeg = rbeg, cend = rend;
-        KSum<T> acc[RPL];
+        // Run accumulation (segmented, plain FMA).  FP32 interleaves two
+        // accumulators so that each sums at most half of a run; the row sums
+        // across groups and tiles are the compensated ones.
+        constexpr int NACC = sizeof(T) == 4 ? 2 : 1;
+        T acc[NACC][RPL];
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) acc[r].zero();
+        for (int h = 0; h < NACC; ++h)
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
         T brow[BR];  // B row of `cur` (loaded once per row, not per nonzero)
         int32_t brow_row = -1;
 #pragma unroll
@@ -346,7 +353,7 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
         auto flush = [&](int32_t frow, int64_t fbeg, int64_t fend, const T(&bq)[BR]) {
             T v[RPL];
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) v[r] = acc[r].value();
+            for (int r = 0; r < RPL; ++r) v[r] = NACC == 2 ? acc[0][r] + acc[NACC - 1][r] : acc[0][r];
             if (fbeg >= ga && fend <= gb) {
                 store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
                 if (OP == OP_PHI) {
@@ -466,10 +473,12 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
                             cbeg = rb[u];
                             cend = re[u];
 #pragma unroll
-                            for (int r = 0; r < RPL; ++r) acc[r].zero();
+                            for (int h = 0; h < NACC; ++h)
+#pragma unroll
+                                for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
                         }
 #pragma unroll
-                        for (int r = 0; r < RPL; ++r) acc[r].fma_add(v[u], pi[u][r]);
+                        for (int r = 0; r < RPL; ++r) acc[u % NACC][r] = fma(v[u], pi[u][r], acc[u % NACC][r]);
                     }
                 }
             }

@@ -241,6 +241,61 @@ def test_solve_resumes_across_calls():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_checkpoint_resume_is_bit_identical(precision):
+    """Stop after two outer iterations, restore the state into a new context,
+    continue: the same bits as running on without stopping (S included)."""
+    T = case("c3s")
+    lam, fs = model_for(T, 25)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) as t:
+        t.set_model(lam, fs)
+        t.mu_solve(1e-4, 2, 4)
+        state = cpapr.cpapr_get_state(t.ctx)
+        r1 = t.mu_solve(1e-4, 2, 4)
+        a = t.get_model()
+    assert state["outer_done"] == 2
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) as u:
+        cpapr.cpapr_set_state(u.ctx, state)
+        r2 = u.mu_solve(1e-4, 2, 4)
+        b = u.get_model()
+    assert r1 == r2
+    assert np.array_equal(a[0], b[0])
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+
+
+def test_injected_allocation_failure_is_clean(monkeypatch):
+    """A failing device allocation (injected on the host) surfaces as
+    CPAPR_E_NOMEM from cpapr_create and leaves the library usable."""
+    T = case("c1")
+    for k in (1, 5, 12):
+        monkeypatch.setenv("CPAPR_FAULT_ALLOC_AT", str(k))
+        with pytest.raises(cpapr.CpaprError) as e:
+            cpapr.Tensor(T.dims, T.idx, T.vals, T.rank)
+        assert e.value.status == 4 and "injected" in str(e.value)
+    monkeypatch.delenv("CPAPR_FAULT_ALLOC_AT")
+    lam, fs = model_for(T)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.set_model(lam, fs)
+        want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[0] * lam[None, :], 0)
+        assert max_rel(t.phi(0), want) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)])
+def test_autotuned_context_matches_oracle(precision, tol):
+    """The autotuner times (lanes, tile, reduction) per mode on the tensor and
+    keeps the fastest; whatever it picks must give the same Phi."""
+    T = case("c2s")
+    lam, fs = model_for(T, 26)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, autotune=1) as t:
+        info = t.info()
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            assert info.tile_nnz[n] in (1024, 2048, 4096, 8192)
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= tol
+
+
 def test_init_random_matches_oracle():
     T = case("c1")
     lo, fo = oracle.init_random(T.dims, T.rank, 4242)
