@@ -165,7 +165,10 @@ static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile,
     (void)n;
 }
 
+void batch_forget(cpapr_ctx *ctx);
+
 cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int reduction) {
+    batch_forget(ctx);
     if (!phi_config_supported((int)ctx->esize, ctx->N - 1, ctx->Rp, lanes))
         return fail(ctx, CPAPR_E_ARG, "rank_lanes not supported for this rank and precision");
     if (tile < 64 || tile > (1 << 20)) return fail(ctx, CPAPR_E_ARG, "tile_nnz must lie in [64, 2^20]");
@@ -220,6 +223,7 @@ const char *cpapr_last_error(const cpapr_ctx *ctx) {
 
 void cpapr_destroy(cpapr_ctx *ctx) {
     if (!ctx) return;
+    batch_forget(ctx);
     cudaStreamSynchronize(ctx->stream);
     for (int n = 0; n < ctx->N; ++n) {
         ModeLayout &L = ctx->mode[n];
@@ -429,7 +433,12 @@ cpapr_status cpapr_set_state(cpapr_ctx *ctx, const double *lambda, const double 
     if (phi_prev) {
         CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, 16, ctx->stream));
         for (int m = 0; m < ctx->N; ++m)
-            if (phi_prev[m]) CPAPR_TRY(upload_matrix(ctx, phi_prev[m], ctx->dims[m], ctx->Phi[m]));
+            if (phi_prev[m]) {
+                CPAPR_TRY(upload_matrix(ctx, phi_prev[m], ctx->dims[m], ctx->Phi[m]));
+                // Phi rows of empty slices are zero by definition (and the
+                // kernels rely on it)
+                CPAPR_TRY(launch_zero_empty(ctx, m, ctx->Phi[m]));
+            }
         int32_t flags[4] = {0, 0, 0, 0};
         CPAPR_CUDA(ctx, cudaMemcpyAsync(flags, ctx->errflag, 16, cudaMemcpyDeviceToHost, ctx->stream));
         CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "phi_kernels.cuh"
@@ -28,7 +29,7 @@
 namespace cpapr {
 
 cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int reduction);
-cpapr_status launch_loglik_host(cpapr_ctx *ctx, double *host);
+cpapr_status loglik_enqueue(cpapr_ctx *ctx, double *host);
 
 namespace {
 
@@ -44,7 +45,11 @@ struct BatchTensor {
     double *colpart;     // [nchunks][rp] column-sum partials
     int32_t chunk0, nchunks;
     double kappa, kappa_tol;
+    const int32_t *erows;  // rows of mode n without nonzeros
+    int64_t nempty;
 };
+
+constexpr int kEmptyChunk = 8192;  // (row, rank) elements per empty-row work item
 
 struct BatchCtl {
     unsigned int tile_next, tile_exit, upd_blocks, active;
@@ -169,6 +174,25 @@ __global__ void __launch_bounds__(256) batch_sb_kernel(const BatchTensor *__rest
     }
 }
 
+// KKT term of the empty rows for the first inner iteration (see empty_kkt_kernel).
+template <typename T>
+__global__ void __launch_bounds__(256) batch_empty_kkt_kernel(const BatchTensor *__restrict__ desc,
+                                                              const int2 *__restrict__ items,
+                                                              const int32_t *__restrict__ flags) {
+    __shared__ double red[8];
+    const int2 w = items[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    if (flags[2 * w.x]) return;
+    const int Rp = d.rp;
+    const int64_t q0 = (int64_t)w.y * kEmptyChunk;
+    const int64_t q1 = min(q0 + kEmptyChunk, d.nempty * Rp);
+    const T *B = reinterpret_cast<const T *>(d.a.B);
+    T v = T(0);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+        v = tmax(v, viol_t(B[(int64_t)d.erows[q / Rp] * Rp + q % Rp], T(0)));
+    publish_kkt<256>((double)v, d.a.inner, red);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__restrict__ desc,
                                                            const int2 *__restrict__ chunks, unsigned int *chunk_count,
@@ -290,8 +314,8 @@ __global__ void gather_states_kernel(InnerState *const *src, int n, InnerState *
 // ---------------------------------------------------------------------------
 struct ModePlan {
     BatchTensor *desc = nullptr;
-    int2 *tiles = nullptr, *splits = nullptr, *chunks = nullptr;
-    int ntiles = 0, nsplits = 0, nchunks = 0;
+    int2 *tiles = nullptr, *splits = nullptr, *chunks = nullptr, *echunks = nullptr;
+    int ntiles = 0, nsplits = 0, nchunks = 0, nechunks = 0;
     cudaGraphExec_t exec = nullptr;
     int body_kernels = 0;
 };
@@ -305,7 +329,16 @@ struct Plan {
     InnerState **state_ptrs = nullptr;
     InnerState *states = nullptr;
     std::vector<void *> owned;
+    // what the plan was built for (it is reused while these match)
+    std::vector<cpapr_ctx *> key;
+    double tol = 0.0;
+    int max_inner = 0, graph = 0, esize = 0, grid = 0;
 };
+
+// The last plan is kept: building it (work lists, descriptors, three graph
+// instantiations) costs milliseconds, a step of a small batch about as much.
+std::mutex g_cache_mu;
+Plan *g_cache = nullptr;
 
 template <typename T>
 cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ctl, cudaStream_t s) {
@@ -405,6 +438,14 @@ void free_plan(Plan &P) {
     P.owned.clear();
 }
 
+void drop_cache_locked() {
+    if (g_cache) {
+        free_plan(*g_cache);
+        delete g_cache;
+        g_cache = nullptr;
+    }
+}
+
 template <typename T>
 cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
                            cpapr_result *results) {
@@ -424,8 +465,16 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         }
         CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
     }
-    Plan P;
-    P.modes.resize(N);
+    std::lock_guard<std::mutex> cache_lock(g_cache_mu);
+    const int graph_flag = c0->opt.use_graph != 0 ? 1 : 0;
+    const std::vector<cpapr_ctx *> key(ctxs, ctxs + count);
+    const bool hit = g_cache && g_cache->key == key && g_cache->tol == tol && g_cache->max_inner == max_inner &&
+                     g_cache->graph == graph_flag && g_cache->esize == (int)sizeof(T);
+    if (!hit) {
+        drop_cache_locked();
+        g_cache = new Plan();
+    }
+    Plan &P = *g_cache;
     auto dalloc = [&](void **p, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
         if (e == cudaSuccess) P.owned.push_back(*p);
@@ -435,10 +484,17 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
     do {                                            \
         cudaError_t _e = (call);                    \
         if (_e != cudaSuccess) {                    \
-            free_plan(P);                           \
+            drop_cache_locked();                    \
             return cuda_fail(c0, _e, #call);        \
         }                                           \
     } while (0)
+    if (!hit) {
+    P.modes.resize(N);
+    P.key = key;
+    P.tol = tol;
+    P.max_inner = max_inner;
+    P.graph = graph_flag;
+    P.esize = (int)sizeof(T);
     // per-tensor column partial areas (sized for the longest mode)
     std::vector<int64_t> colpart_off(count);
     int64_t colpart_total = 0;
@@ -465,7 +521,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
     for (int n = 0; n < N; ++n) {
         ModePlan &mp = P.modes[n];
         std::vector<BatchTensor> desc(count);
-        std::vector<int2> tiles, chunks;
+        std::vector<int2> tiles, chunks, echunks;
         std::vector<int2> splits;
         for (int i = 0; i < count; ++i) {
             cpapr_ctx *c = ctxs[i];
@@ -509,9 +565,12 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             d.chunk0 = (int32_t)chunks.size();
             d.kappa = c->opt.kappa;
             d.kappa_tol = c->opt.kappa_tol;
+            d.erows = L.erows;
+            d.nempty = c->nnz > 0 ? L.nempty : 0;
             for (int t = 0; t < (c->nnz > 0 ? L.ntiles : 0); ++t) tiles.push_back(make_int2(i, t));
             for (int t = 0; t < (c->nnz > 0 ? L.nsplit : 0); ++t) splits.push_back(make_int2(i, t));
             for (int t = 0; t < d.nchunks; ++t) chunks.push_back(make_int2(i, t));
+            for (int t = 0; t < (int)ceil_div(d.nempty * c->Rp, kEmptyChunk); ++t) echunks.push_back(make_int2(i, t));
         }
         // larger tensors' tiles first: the persistent blocks finish together
         std::stable_sort(tiles.begin(), tiles.end(), [&](const int2 &x, const int2 &y) {
@@ -520,10 +579,14 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         mp.ntiles = (int)tiles.size();
         mp.nsplits = (int)splits.size();
         mp.nchunks = (int)chunks.size();
+        mp.nechunks = (int)echunks.size();
         BT_CUDA(dalloc((void **)&mp.desc, desc.size() * sizeof(BatchTensor)));
         BT_CUDA(dalloc((void **)&mp.tiles, tiles.size() * sizeof(int2)));
         BT_CUDA(dalloc((void **)&mp.splits, splits.size() * sizeof(int2)));
         BT_CUDA(dalloc((void **)&mp.chunks, chunks.size() * sizeof(int2)));
+        BT_CUDA(dalloc((void **)&mp.echunks, echunks.size() * sizeof(int2)));
+        if (!echunks.empty())
+            BT_CUDA(cudaMemcpy(mp.echunks, echunks.data(), echunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.desc, desc.data(), desc.size() * sizeof(BatchTensor), cudaMemcpyHostToDevice));
         if (!tiles.empty())
             BT_CUDA(cudaMemcpy(mp.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -531,16 +594,18 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             BT_CUDA(cudaMemcpy(mp.splits, splits.data(), splits.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
     }
-    const int grid = persistent_grid<T>(N - 1);
-    const bool graph = c0->opt.use_graph != 0;
-    if (graph)
+    P.grid = persistent_grid<T>(N - 1);
+    if (graph_flag)
         for (int n = 0; n < N; ++n) {
-            cpapr_status st = build_graph<T>(c0, P, n, tol, max_inner, grid);
+            cpapr_status st = build_graph<T>(c0, P, n, tol, max_inner, P.grid);
             if (st != CPAPR_OK) {
-                free_plan(P);
+                drop_cache_locked();
                 return st;
             }
         }
+    }  // plan built
+    const int grid = P.grid;
+    const bool graph = graph_flag != 0;
 
     struct Track {
         int outer = 0, total = 0;
@@ -564,6 +629,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             ModePlan &mp = P.modes[n];
             batch_sb_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
             BT_CUDA(cudaGetLastError());
+            if (mp.nechunks > 0) {
+                batch_empty_kkt_kernel<T><<<mp.nechunks, 256, 0, s>>>(mp.desc, mp.echunks, P.flags);
+                BT_CUDA(cudaGetLastError());
+            }
             if (graph) {
                 BT_CUDA(cudaGraphLaunch(mp.exec, s));
             } else {
@@ -609,23 +678,54 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         }
         c0->launches += used_max;
     }
-    free_plan(P);
 #undef BT_CUDA
-    if (st != CPAPR_OK) return st;
+    if (st != CPAPR_OK) {
+        drop_cache_locked();
+        return st;
+    }
+    // final log-likelihoods: every tensor on its own stream after the batch
+    // stream's work, one synchronisation for all
+    std::vector<double> ll(count, 0.0);
+    cudaEvent_t done_ev = nullptr;
+    CPAPR_CUDA(c0, cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(done_ev, s);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctxs[i]->stream, done_ev, 0);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(done_ev);
+        return cuda_fail(c0, e, "batch log-likelihood ordering");
+    }
+    cpapr_status lst = CPAPR_OK;
+    for (int i = 0; i < count && lst == CPAPR_OK; ++i) lst = loglik_enqueue(ctxs[i], &ll[i]);
     for (int i = 0; i < count; ++i) {
-        double ll = 0.0;
-        CPAPR_TRY(launch_loglik_host(ctxs[i], &ll));
+        cudaError_t se = cudaStreamSynchronize(ctxs[i]->stream);
+        if (se != cudaSuccess && lst == CPAPR_OK) lst = cuda_fail(ctxs[i], se, "cudaStreamSynchronize");
+    }
+    cudaEventDestroy(done_ev);
+    if (lst != CPAPR_OK) return lst;
+    for (int i = 0; i < count; ++i) {
         results[i].outer_iters = tr[i].outer;
         results[i].total_inner = tr[i].total;
         results[i].converged = tr[i].conv ? 1 : 0;
         results[i].reserved = 0;
-        results[i].loglik = ll;
+        results[i].loglik = ll[i];
         results[i].kkt_viol = tr[i].kkt;
     }
     return CPAPR_OK;
 }
 
 }  // namespace
+
+// Drops the cached batch plan if it refers to ctx (called when a context is
+// destroyed or its tiling changes).
+void batch_forget(cpapr_ctx *ctx) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    if (!g_cache) return;
+    for (cpapr_ctx *c : g_cache->key)
+        if (c == ctx) {
+            drop_cache_locked();
+            return;
+        }
+}
 
 // Batched solve through the persistent kernels; contexts must share the
 // device, the precision and the number of modes.

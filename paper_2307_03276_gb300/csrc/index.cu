@@ -255,6 +255,17 @@ __global__ void seg_kernel(const uint32_t *__restrict__ skeys, int64_t nnz, int3
     }
 }
 
+__global__ void empty_flags_kernel(const int32_t *__restrict__ seg, int32_t In, uint32_t *__restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < In; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = seg[i] == seg[i + 1] ? 1u : 0u;
+}
+
+__global__ void empty_write_kernel(const int32_t *__restrict__ seg, int32_t In, const uint32_t *__restrict__ pos,
+                                   int32_t *__restrict__ erows) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < In; i += (int64_t)gridDim.x * blockDim.x)
+        if (seg[i] == seg[i + 1]) erows[pos[i]] = (int32_t)i;
+}
+
 __global__ void gather_i32_kernel(const int32_t *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
                                   int32_t *__restrict__ dst) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -392,6 +403,31 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         else
             gather_val_kernel<float><<<grid_for(nnz), 256, 0, s>>>(vals, perm, nnz, (float *)L.val);
         BL_CUDA(cudaGetLastError());
+    }
+    // per mode: the rows without nonzeros (their Phi row is zero)
+    for (int n = 0; n < N; ++n) {
+        ModeLayout &L = ctx->mode[n];
+        uint32_t *flag = nullptr;
+        BL_CUDA(cudaMallocAsync((void **)&flag, (size_t)(L.In + 1) * 4, s));
+        empty_flags_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flag);
+        BL_CUDA(cudaGetLastError());
+        cpapr_status st = exclusive_scan_u32(ctx, flag, L.In, flag + L.In);
+        if (st != CPAPR_OK) {
+            cudaFreeAsync(flag, s);
+            cleanup();
+            return st;
+        }
+        uint32_t total = 0;
+        BL_CUDA(cudaMemcpyAsync(&total, flag + L.In, 4, cudaMemcpyDeviceToHost, s));
+        BL_CUDA(cudaStreamSynchronize(s));
+        L.nempty = (int32_t)total;
+        void *p = nullptr;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)std::max<int32_t>(L.nempty, 1) * 4));
+        L.erows = (int32_t *)p;
+        empty_write_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flag, L.erows);
+        BL_CUDA(cudaGetLastError());
+        count_launch(ctx, 2);
+        BL_CUDA(cudaFreeAsync(flag, s));
     }
     cleanup();
     BL_CUDA(cudaStreamSynchronize(s));

@@ -51,6 +51,8 @@ struct ModeLayout {
     int32_t *row_lo = nullptr;     // [ntiles + 1] first row whose start lies in the tile; row_lo[ntiles] = In
     int32_t nsplit = 0;
     int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
+    int32_t nempty = 0;
+    int32_t *erows = nullptr;      // [nempty] rows without nonzeros, increasing
 };
 
 struct cpapr_ctx_impl;
@@ -153,6 +155,10 @@ enum PhiOp { OP_PHI = 0, OP_MTTKRP = 1, OP_LL = 2 };
 cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner);
 // Sum of x log(m) over nonzeros, into llpart then *dst (device double).
 cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
+// Rows of mode n without nonzeros: zero them in `out`; add their KKT term
+// (first inner iteration) after the S/B kernel.
+cpapr_status launch_zero_empty(cpapr_ctx *ctx, int n, void *out);
+cpapr_status launch_empty_kkt(cpapr_ctx *ctx, int n, const void *B, InnerState *inner);
 bool phi_config_supported(int esize, int nm1, int rp, int lanes);
 
 // ---- MU kernels (mu.cu) -------------------------------------------------------

@@ -101,6 +101,41 @@ static cudaError_t run_kkt_rows(const T *B, const T *P, int64_t n, InnerState *i
     return cudaGetLastError();
 }
 
+static unsigned small_grid(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 4));
+}
+
+// Zeros the rows of mode n that hold no nonzeros (the tile kernels never
+// write them).
+cpapr_status launch_zero_empty(cpapr_ctx *ctx, int n, void *out) {
+    const ModeLayout &L = ctx->mode[n];
+    if (L.nempty == 0) return CPAPR_OK;
+    const int64_t m = (int64_t)L.nempty * ctx->Rp;
+    if (ctx->esize == 8)
+        zero_rows_kernel<double><<<small_grid(m), 256, 0, ctx->stream>>>(L.erows, L.nempty, ctx->Rp, (double *)out);
+    else
+        zero_rows_kernel<float><<<small_grid(m), 256, 0, ctx->stream>>>(L.erows, L.nempty, ctx->Rp, (float *)out);
+    count_launch(ctx);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
+// KKT term of the empty rows for the first inner iteration (after S and B).
+cpapr_status launch_empty_kkt(cpapr_ctx *ctx, int n, const void *B, InnerState *inner) {
+    const ModeLayout &L = ctx->mode[n];
+    if (L.nempty == 0 || ctx->nnz == 0 || L.reduction == CPAPR_REDUCE_ATOMIC) return CPAPR_OK;
+    const int64_t m = (int64_t)L.nempty * ctx->Rp;
+    if (ctx->esize == 8)
+        empty_kkt_kernel<double><<<small_grid(m), 256, 0, ctx->stream>>>(L.erows, L.nempty, ctx->Rp,
+                                                                         (const double *)B, inner);
+    else
+        empty_kkt_kernel<float><<<small_grid(m), 256, 0, ctx->stream>>>(L.erows, L.nempty, ctx->Rp,
+                                                                        (const float *)B, inner);
+    count_launch(ctx);
+    CPAPR_CUDA(ctx, cudaGetLastError());
+    return CPAPR_OK;
+}
+
 cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner) {
     ModeLayout &L = ctx->mode[n];
     const int64_t nel = (int64_t)L.In * ctx->Rp;
@@ -108,6 +143,10 @@ cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *ou
     const bool atomic = a.atomic && op != OP_LL;
     if (ctx->nnz == 0 || atomic) {
         CPAPR_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)nel * ctx->esize, ctx->stream));
+    } else if (op != OP_LL && out != ctx->Phi[n]) {
+        // a shared output buffer: clear this mode's empty rows.  Phi[n] keeps
+        // them zero from the moment the model is set.
+        CPAPR_TRY(launch_zero_empty(ctx, n, out));
     }
     if (ctx->nnz > 0) {
         ProfScope ps(ctx, op == OP_MTTKRP ? K_MTTKRP : K_PHI);
@@ -141,6 +180,7 @@ cpapr_status launch_phi_given_carry(cpapr_ctx *ctx, int n, const void *B, void *
     a.atomic = 0;
     a.carry = carry;
     if (ctx->nnz == 0) return fail(ctx, CPAPR_E_ARG, "empty tensor");
+    CPAPR_TRY(launch_zero_empty(ctx, n, out));
     cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_PHI);
     count_launch(ctx);
     if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");

@@ -388,10 +388,15 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k)
                     if (k < nm1) ii[u][k] = __ldg(a.idx[k] + qq);
-                while (qq >= rend) {
+                if (qq >= rend) {  // next row; jump over empty rows by bisection
                     ++row;
                     rbeg = rend;
                     rend = __ldg(seg + row + 1);
+                    if (qq >= rend) {
+                        row = ub_seg(seg, row + 1, a.row_lo[t + 1], qq) - 1;
+                        rbeg = __ldg(seg + row);
+                        rend = __ldg(seg + row + 1);
+                    }
                 }
                 rr[u] = row;
                 rb[u] = rbeg;
@@ -535,16 +540,10 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
                 }
             }
         }
-        // rows owned by this tile that hold no nonzero: Phi row = 0
-        const int32_t rlo = a.row_lo[t], rhi = a.row_lo[t + 1];
-        for (int32_t i = rlo + warp; i < rhi; i += NWARPS) {
-            if (__ldg(seg + i) == __ldg(seg + i + 1)) {
-                for (int c = wlane; c < Rp; c += 32) {
-                    out[(int64_t)i * Rp + c] = T(0);
-                    if (OP == OP_PHI) kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)i * Rp + c), T(0)));
-                }
-            }
-        }
+        // Rows without nonzeros are never written here: their Phi row is zero
+        // in a buffer that starts zeroed, and their KKT term min(B, 1) is
+        // added once per inner loop by empty_kkt_kernel (after the first
+        // update those B rows are zero).
     }
     if (OP == OP_PHI && a.inner && !a.atomic) publish_kkt<THREADS>(kkt, a.inner, red);
 }
@@ -606,6 +605,29 @@ __global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
     __shared__ T sm_c[256];
     __shared__ double red[8];
     phi_fixup_body<T, OP>(a, blockIdx.x, sm_s, sm_c, red);
+}
+
+// KKT term of the rows without nonzeros, |min(B, 1 - 0)|, published into
+// the slot of the first inner iteration (run after the S/B kernel, which
+// cleared that slot).  Later iterations need no term: the first update sets
+// those B rows to B * 0 = 0.
+template <typename T>
+__global__ void __launch_bounds__(256) empty_kkt_kernel(const int32_t *__restrict__ erows, int64_t nempty, int Rp,
+                                                         const T *__restrict__ B, InnerState *inner) {
+    __shared__ double red[8];
+    T v = T(0);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nempty * Rp;
+         q += (int64_t)gridDim.x * blockDim.x)
+        v = tmax(v, viol_t(B[(int64_t)erows[q / Rp] * Rp + q % Rp], T(0)));
+    publish_kkt<256>((double)v, inner, red);
+}
+
+// Writes zeros into the rows without nonzeros.
+template <typename T>
+__global__ void zero_rows_kernel(const int32_t *__restrict__ erows, int64_t nempty, int Rp, T *__restrict__ out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nempty * Rp;
+         q += (int64_t)gridDim.x * blockDim.x)
+        out[(int64_t)erows[q / Rp] * Rp + q % Rp] = T(0);
 }
 
 // KKT violation over all rows (used after the atomic reduction).

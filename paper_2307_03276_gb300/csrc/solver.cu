@@ -85,6 +85,7 @@ static cpapr_status build_inner_graph(cpapr_ctx *ctx, int n, double tol, int max
 static cpapr_status enqueue_mode(cpapr_ctx *ctx, int n, double tol, int max_inner, bool shift) {
     InnerState *inner = ctx->inner + n;
     CPAPR_TRY(launch_sb(ctx, n, shift, inner));
+    CPAPR_TRY(launch_empty_kkt(ctx, n, ctx->B, inner));
     if (ctx->opt.use_graph) {
         CPAPR_TRY(build_inner_graph(ctx, n, tol, max_inner));
         CPAPR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec[n], ctx->stream));
@@ -98,11 +99,18 @@ static cpapr_status enqueue_mode(cpapr_ctx *ctx, int n, double tol, int max_inne
     return CPAPR_OK;
 }
 
-static cpapr_status loglik_now(cpapr_ctx *ctx, double *host) {
+// Enqueues the log-likelihood of the current model and its copy to *host
+// (complete after the context's stream is synchronised).
+cpapr_status loglik_enqueue(cpapr_ctx *ctx, double *host) {
     CPAPR_TRY(launch_scale_b(ctx, 0, ctx->B));
     CPAPR_TRY(launch_loglik(ctx, ctx->B, ctx->scalars));
     CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(host, ctx->scalars, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    return CPAPR_OK;
+}
+
+static cpapr_status loglik_now(cpapr_ctx *ctx, double *host) {
+    CPAPR_TRY(loglik_enqueue(ctx, host));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CPAPR_OK;
 }
