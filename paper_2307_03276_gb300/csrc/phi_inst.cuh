@@ -23,7 +23,7 @@ constexpr int kThreads = sizeof(PHI_T) == 8 ? 128 : 256;
 // ranks per lane has no registers to spare for a second batch entry.
 template <int RPL, int G>
 constexpr int unroll_for() {
-    if (sizeof(PHI_T) == 8) return RPL >= 32 ? 1 : (G >= 2 ? 2 : 1);
+    if (sizeof(PHI_T) == 8) return RPL >= 16 ? (G >= 2 ? 2 : 1) : (G >= 4 ? 4 : (G >= 2 ? 2 : 1));
     return G >= 4 ? 4 : 2;
 }
 

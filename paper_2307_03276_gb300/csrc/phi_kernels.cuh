@@ -327,7 +327,7 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
     // B rows held in registers (reused along a row), except for wide FP64
     // lanes, whose registers go to the Khatri-Rao row and the accumulator:
     // there the dot reads the B row through L1 for every nonzero
-    constexpr bool BREG = !(sizeof(T) == 8 && RPL >= 16);
+    constexpr bool BREG = !(sizeof(T) == 8 && (RPL >= 16 || U >= 4));
     constexpr int BR = BREG ? RPL : 1;
 
     if (ga < gb) {
