@@ -29,9 +29,11 @@
 // whoever writes a final Phi row also reduces its violation, and one atomicMax
 // per block publishes it (non-negative doubles order like their bit patterns).
 //
-// FP32 form: gathers, Khatri-Rao products, dot and scale in FP32; every
-// row sum (run accumulation, chain and carry sums) is Kahan-compensated;
-// the violation and the log-likelihood are reduced in FP64.
+// FP32 form: gathers, Khatri-Rao products, dot and scale in FP32; a run of
+// same-row nonzeros is summed in plain FP32 over two interleaved
+// accumulators, the sums of partial rows across groups and tiles are
+// Kahan-compensated; the violation is taken in FP32 (its maximum is exact)
+// and published, like the log-likelihood partials, in FP64.
 #pragma once
 
 #include <cuda_runtime.h>
