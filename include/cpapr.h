@@ -69,7 +69,10 @@ enum { CPAPR_REDUCE_AUTO = 0, CPAPR_REDUCE_ATOMIC = 1, CPAPR_REDUCE_SEGMENTED = 
  *             the previous Phi(i,r) > 1 (defaults 0.01, 1e-10).
  *  seed       reserved for callers; cpapr_init_random takes its own seed.
  *  stream     a cudaStream_t to run on, or NULL for a stream the context owns.
- *  tile_nnz   nonzeros per tile (one thread block); 0 = automatic.
+ *  tile_nnz   nonzeros per tile (one thread block); 0 = automatic.  A
+ *             multiple of 4 in [64, 2^20] whose staged index and value
+ *             streams fit in shared memory (about 220 KB per block, e.g. at
+ *             most 8192 for a 3-way FP64 tensor); E_ARG otherwise.
  *  rank_lanes lanes that share one nonzero (1..32, power of two); 0 = automatic.
  *  use_graph  1 = run each mode's inner loop as a CUDA graph with a device-side
  *             early exit (default), 0 = plain stream launches.

@@ -146,9 +146,9 @@ static int next_pow2(int v) {
 // Built-in choice of lanes per nonzero and nonzeros per tile (from sweeps on
 // GB300 over the 1e7-nonzero 3-way and 5e7-nonzero 4-way workloads).  FP64:
 // one lane per nonzero up to 16 ranks (no shuffle adds on the scarce FP64
-// pipe), 8 ranks per lane above with batches of two nonzeros; FP32: 16-byte
-// vectors of 4 ranks per lane up to 32 ranks, 8 ranks per lane above, and
-// larger tiles for large tensors (fewer rows cut across tiles).
+// pipe), 8 ranks per lane above with batches of four nonzeros; FP32: 16-byte
+// vectors of 4 ranks per lane up to 32 ranks, 8 ranks per lane above, and the
+// largest tile whose shared-memory stage leaves room for three blocks per SM.
 static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
     const int Rp = ctx->Rp;
     int g;
@@ -157,10 +157,17 @@ static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile,
     else
         g = Rp <= 32 ? std::max(1, Rp / 4) : Rp / 8;
     *lanes = g;
-    if (ctx->esize == 8)
+    if (ctx->esize == 8) {
         *tile = Rp <= 16 ? 2048 : 1024;
-    else
-        *tile = ctx->nnz >= 30000000 ? 8192 : 4096;
+    } else {
+        // the largest tile whose shared-memory stage still lets three blocks share an SM
+        *tile = 1024;
+        for (int t : {4096, 2048})
+            if (phi_smem_for(4, ctx->N - 1, t, Rp, g) <= 74 * 1024) {
+                *tile = t;
+                break;
+            }
+    }
     *reduction = CPAPR_REDUCE_SEGMENTED;
     (void)n;
 }
@@ -171,7 +178,10 @@ cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int redu
     batch_forget(ctx);
     if (!phi_config_supported((int)ctx->esize, ctx->N - 1, ctx->Rp, lanes))
         return fail(ctx, CPAPR_E_ARG, "rank_lanes not supported for this rank and precision");
-    if (tile < 64 || tile > (1 << 20)) return fail(ctx, CPAPR_E_ARG, "tile_nnz must lie in [64, 2^20]");
+    if (tile < 64 || tile > (1 << 20) || tile % 4)
+        return fail(ctx, CPAPR_E_ARG, "tile_nnz must be a multiple of 4 in [64, 2^20]");
+    if (phi_smem_for((int)ctx->esize, ctx->N - 1, tile, ctx->Rp, lanes) > kMaxPhiSmem)
+        return fail(ctx, CPAPR_E_ARG, "tile_nnz too large: its staged streams and partial rows exceed shared memory");
     ModeLayout &L = ctx->mode[n];
     L.lanes = lanes;
     L.reduction = reduction == CPAPR_REDUCE_ATOMIC ? CPAPR_REDUCE_ATOMIC : CPAPR_REDUCE_SEGMENTED;
@@ -228,7 +238,6 @@ void cpapr_destroy(cpapr_ctx *ctx) {
     for (int n = 0; n < ctx->N; ++n) {
         ModeLayout &L = ctx->mode[n];
         if (L.row_first) cudaFree(L.row_first);
-        if (L.row_lo) cudaFree(L.row_lo);
         if (L.split) cudaFree(L.split);
         if (ctx->graph_exec[n]) cudaGraphExecDestroy(ctx->graph_exec[n]);
     }
@@ -266,8 +275,8 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
     if (!(o.eps > 0.0) || !(o.kappa >= 0.0) || !(o.kappa_tol >= 0.0)) return fail(nullptr, CPAPR_E_ARG, "bad eps/kappa");
     if (o.rank_lanes < 0 || o.rank_lanes > 32 || (o.rank_lanes & (o.rank_lanes - 1)))
         return fail(nullptr, CPAPR_E_ARG, "rank_lanes must be 0 or a power of two <= 32");
-    if (o.tile_nnz != 0 && (o.tile_nnz < 64 || o.tile_nnz > (1 << 20)))
-        return fail(nullptr, CPAPR_E_ARG, "tile_nnz must be 0 or lie in [64, 2^20]");
+    if (o.tile_nnz != 0 && (o.tile_nnz < 64 || o.tile_nnz > (1 << 20) || o.tile_nnz % 4))
+        return fail(nullptr, CPAPR_E_ARG, "tile_nnz must be 0 or a multiple of 4 in [64, 2^20]");
 
     cpapr_ctx *ctx = new (std::nothrow) cpapr_ctx();
     if (!ctx) return fail(nullptr, CPAPR_E_NOMEM, "host allocation failed");
@@ -451,6 +460,18 @@ cpapr_status cpapr_set_state(cpapr_ctx *ctx, const double *lambda, const double 
     return CPAPR_OK;
 }
 
+// After a call's last synchronisation: did a bounded device-side wait give
+// up?  (errflag[3]; a call without one, such as cpapr_phi_noalloc, leaves it
+// for the next call that checks.)
+static cpapr_status check_waits(cpapr_ctx *ctx) {
+    int32_t f = 0;
+    CPAPR_CUDA(ctx, cudaMemcpyAsync(&f, ctx->errflag + 3, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!f) return CPAPR_OK;
+    CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag + 3, 0, 4, ctx->stream));
+    return fail(ctx, CPAPR_E_TIMEOUT, "a device-side staging wait gave up; the results of this call are incomplete");
+}
+
 static cpapr_status check_mode(cpapr_ctx *ctx, int32_t mode) {
     if (mode < 0 || mode >= ctx->N) return fail(ctx, CPAPR_E_ARG, "mode out of range");
     if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
@@ -472,7 +493,7 @@ cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *ou
     CPAPR_TRY(launch_phi(ctx, mode, OP_PHI, ctx->B, ctx->outbuf, nullptr));
     CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return CPAPR_OK;
+    return check_waits(ctx);
 }
 
 cpapr_status cpapr_mttkrp(cpapr_ctx *ctx, int32_t mode, double *out) {
@@ -482,7 +503,7 @@ cpapr_status cpapr_mttkrp(cpapr_ctx *ctx, int32_t mode, double *out) {
     CPAPR_TRY(launch_phi(ctx, mode, OP_MTTKRP, nullptr, ctx->outbuf, nullptr));
     CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return CPAPR_OK;
+    return check_waits(ctx);
 }
 
 cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
@@ -494,7 +515,7 @@ cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
     CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(out, ctx->scalars, 8, cudaMemcpyDefault, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return CPAPR_OK;
+    return check_waits(ctx);
 }
 
 cpapr_status cpapr_mu_solve(cpapr_ctx *ctx, double tol, int32_t max_outer, int32_t max_inner, cpapr_result *res,
@@ -503,7 +524,8 @@ cpapr_status cpapr_mu_solve(cpapr_ctx *ctx, double tol, int32_t max_outer, int32
     if (!res) return fail(ctx, CPAPR_E_ARG, "res is NULL");
     if (max_outer < 0 || max_inner < 1 || !(tol >= 0.0)) return fail(ctx, CPAPR_E_ARG, "bad tol / iteration bounds");
     if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
-    return mu_solve(ctx, tol, max_outer, max_inner, res, inner_trace, ll_trace);
+    CPAPR_TRY(mu_solve(ctx, tol, max_outer, max_inner, res, inner_trace, ll_trace));
+    return check_waits(ctx);
 }
 
 cpapr_status cpapr_batch_mu_solve(cpapr_ctx *const *ctxs, int32_t count, double tol, int32_t max_outer,
@@ -516,7 +538,10 @@ cpapr_status cpapr_batch_mu_solve(cpapr_ctx *const *ctxs, int32_t count, double 
         if (ctxs[i]->esize != ctxs[0]->esize) return fail(nullptr, CPAPR_E_ARG, "mixed precisions in a batch");
     }
     if (max_outer < 0 || max_inner < 1 || !(tol >= 0.0)) return fail(nullptr, CPAPR_E_ARG, "bad tol / iteration bounds");
-    return batch_mu_solve(ctxs, count, tol, max_outer, max_inner, results);
+    const cpapr_status st = batch_mu_solve(ctxs, count, tol, max_outer, max_inner, results);
+    if (st != CPAPR_OK) return st;
+    for (int i = 0; i < count; ++i) CPAPR_TRY(check_waits(ctxs[i]));
+    return CPAPR_OK;
 }
 
 cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info) {

@@ -87,20 +87,27 @@ template <typename T> __host__ __device__ constexpr int batch_threads() { return
 template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 2; }
 
 template <typename T, int NM1, int K>
-__device__ __forceinline__ void run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red) {
+__device__ __forceinline__ bool run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red, uint64_t *bar,
+                                          uint32_t &phase) {
     constexpr int RPL = Classes<T>::rpl[K];
     constexpr int G = Classes<T>::g[K];
-    phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>()>(a, tile, smem, red);
+    return phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>()>(a, tile, smem, red,
+                                                                                               bar, phase);
 }
 
 template <typename T, int NM1>
 __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) batch_phi_kernel(const BatchTensor *__restrict__ desc,
                                                                        const int2 *__restrict__ items, int nitems,
                                                                        BatchCtl *ctl) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[batch_threads<T>() / 32];
     __shared__ int s_item;
-    for (;;) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) stage_barrier_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    bool ok = true;
+    while (ok) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(&ctl->tile_next, 1u);
         __syncthreads();
         const int it = s_item;
@@ -109,12 +116,13 @@ __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) bat
         const int2 w = items[it];
         const PhiArgs a = desc[w.x].a;
         switch (desc[w.x].cfg) {
-            case 0: run_class<T, NM1, 0>(a, w.y, smem_raw, red); break;
-            case 1: run_class<T, NM1, 1>(a, w.y, smem_raw, red); break;
-            case 2: run_class<T, NM1, 2>(a, w.y, smem_raw, red); break;
-            case 3: run_class<T, NM1, 3>(a, w.y, smem_raw, red); break;
+            case 0: ok = run_class<T, NM1, 0>(a, w.y, smem_raw, red, &bar, phase); break;
+            case 1: ok = run_class<T, NM1, 1>(a, w.y, smem_raw, red, &bar, phase); break;
+            case 2: ok = run_class<T, NM1, 2>(a, w.y, smem_raw, red, &bar, phase); break;
+            case 3: ok = run_class<T, NM1, 3>(a, w.y, smem_raw, red, &bar, phase); break;
             default:
-                if constexpr (Classes<T>::n > 4) run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0)>(a, w.y, smem_raw, red);
+                if constexpr (Classes<T>::n > 4)
+                    ok = run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0)>(a, w.y, smem_raw, red, &bar, phase);
                 break;
         }
     }
@@ -318,6 +326,7 @@ struct ModePlan {
     int ntiles = 0, nsplits = 0, nchunks = 0, nechunks = 0;
     cudaGraphExec_t exec = nullptr;
     int body_kernels = 0;
+    size_t smem = 0;  // dynamic shared memory of the Phi launch (largest tile of the batch)
 };
 
 struct Plan {
@@ -342,9 +351,7 @@ Plan *g_cache = nullptr;
 
 template <typename T>
 cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ctl, cudaStream_t s) {
-    int maxrpl = 0;
-    for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
-    const size_t smem = (size_t)2 * batch_threads<T>() * maxrpl * sizeof(T) + (size_t)2 * batch_threads<T>() * 4;
+    const size_t smem = mp.smem;
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, batch_threads<T>(), smem, s>>>(mp.desc, mp.tiles, mp.ntiles, ctl);
@@ -359,13 +366,10 @@ cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ct
 }
 
 template <typename T>
-int persistent_grid(int nm1) {
+int persistent_grid(int nm1, size_t smem) {
     int dev = 0, sms = 152, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int maxrpl = 0;
-    for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
-    const size_t smem = (size_t)2 * batch_threads<T>() * maxrpl * sizeof(T) + (size_t)2 * batch_threads<T>() * 4;
     const void *k = nm1 == 2 ? (const void *)batch_phi_kernel<T, 2>
                              : nm1 == 3 ? (const void *)batch_phi_kernel<T, 3>
                                         : nm1 == 4 ? (const void *)batch_phi_kernel<T, 4> : (const void *)batch_phi_kernel<T, 0>;
@@ -518,6 +522,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             for (int n = 0; n < N; ++n) sp[(size_t)i * N + n] = ctxs[i]->inner + n;
         BT_CUDA(cudaMemcpy(P.state_ptrs, sp.data(), sp.size() * sizeof(InnerState *), cudaMemcpyHostToDevice));
     }
+    size_t smem_max = 0;
     for (int n = 0; n < N; ++n) {
         ModePlan &mp = P.modes[n];
         std::vector<BatchTensor> desc(count);
@@ -536,7 +541,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.In = L.In;
             a.nm1 = c->N - 1;
             a.atomic = 0;
-            a.seg = L.seg;
+            a.rid = L.rid;
             int k = 0;
             for (int m = 0; m < N; ++m) {
                 if (m == n) continue;
@@ -548,13 +553,12 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.B = c->B;
             a.out = c->Phi[n];
             a.carry = c->carry;
-            a.row_first = L.row_first;
-            a.row_lo = L.row_lo;
             a.split = L.split;
             a.nsplit = L.nsplit;
             a.eps = c->opt.eps;
             a.inner = c->inner + n;
             a.llpart = c->llpart;
+            a.err = c->errflag + 3;
             d.cfg = class_for<T>(c->Rp);
             d.rp = c->Rp;
             d.rows = c->dims[n];
@@ -577,6 +581,13 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             return ctxs[x.x]->nnz > ctxs[y.x]->nnz;
         });
         mp.ntiles = (int)tiles.size();
+        {
+            int maxrpl = 0, maxtile = 4;
+            for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
+            for (int i = 0; i < count; ++i) maxtile = std::max(maxtile, ctxs[i]->mode[n].tile_nnz);
+            mp.smem = phi_smem_bytes(maxtile, N - 1, (int)sizeof(T), batch_threads<T>(), maxrpl);
+            smem_max = std::max(smem_max, mp.smem);
+        }
         mp.nsplits = (int)splits.size();
         mp.nchunks = (int)chunks.size();
         mp.nechunks = (int)echunks.size();
@@ -594,7 +605,12 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             BT_CUDA(cudaMemcpy(mp.splits, splits.data(), splits.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
     }
-    P.grid = persistent_grid<T>(N - 1);
+    if (smem_max > kMaxPhiSmem) {
+        drop_cache_locked();
+        return fail(c0, CPAPR_E_ARG, "batch: tile_nnz too large for the shared-memory stage");
+    }
+    for (int n = 0; n < N; ++n) P.modes[n].smem = smem_max;  // one occupancy for the whole plan
+    P.grid = persistent_grid<T>(N - 1, smem_max);
     if (graph_flag)
         for (int n = 0; n < N; ++n) {
             cpapr_status st = build_graph<T>(c0, P, n, tol, max_inner, P.grid);

@@ -367,6 +367,9 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         void *p = nullptr;
         BL_TRY(dev_alloc(ctx, &p, (size_t)(L.In + 1) * 4));
         L.seg = (int32_t *)p;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
+        L.rid = (int32_t *)p;
+        BL_CUDA(cudaMemsetAsync(p, 0xff, (size_t)np * 4, s));  // -1: no row past the last nonzero
         int k = 0;
         for (int m = 0; m < N; ++m) {
             if (m == n) continue;
@@ -391,6 +394,7 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         BL_TRY(radix_sort(ctx, keys, perm, tk, tv, nnz, bits));
         seg_kernel<<<grid_for(nnz), 256, 0, s>>>(keys, nnz, L.In, L.seg);
         BL_CUDA(cudaGetLastError());
+        BL_CUDA(cudaMemcpyAsync(L.rid, keys, nnz * 4, cudaMemcpyDeviceToDevice, s));
         k = 0;
         for (int m = 0; m < N; ++m) {
             if (m == n) continue;
@@ -451,29 +455,11 @@ __device__ __forceinline__ int32_t upper_bound_seg(const int32_t *seg, int32_t l
     return lo;
 }
 
-__device__ __forceinline__ int32_t lower_bound_seg(const int32_t *seg, int32_t lo, int32_t hi, int64_t p) {
-    // first i in [lo, hi) with seg[i] >= p (hi if none)
-    while (lo < hi) {
-        int32_t mid = lo + ((hi - lo) >> 1);
-        if ((int64_t)seg[mid] >= p)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
-}
-
-__global__ void tile_rows_kernel(const int32_t *__restrict__ seg, int32_t In, int64_t nnz, int32_t T, int32_t ntiles,
-                                 int32_t *__restrict__ row_first, int32_t *__restrict__ row_lo) {
+__global__ void tile_rows_kernel(const int32_t *__restrict__ seg, int32_t In, int32_t T, int32_t ntiles,
+                                 int32_t *__restrict__ row_first) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > ntiles) return;
-    int64_t p0 = (int64_t)t * T;
-    if (t < ntiles) {
-        row_first[t] = upper_bound_seg(seg, 0, In, p0) - 1;
-        row_lo[t] = lower_bound_seg(seg, 0, In, p0);
-    } else {
-        row_lo[t] = In;
-    }
+    if (t >= ntiles) return;
+    row_first[t] = upper_bound_seg(seg, 0, In, (int64_t)t * T) - 1;
 }
 
 __global__ void split_flags_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ row_first, int32_t T,
@@ -509,18 +495,15 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     ModeLayout &L = ctx->mode[n];
     cudaStream_t s = ctx->stream;
     if (L.row_first) cudaFreeAsync(L.row_first, s);
-    if (L.row_lo) cudaFreeAsync(L.row_lo, s);
     if (L.split) cudaFreeAsync(L.split, s);
-    L.row_first = L.row_lo = L.split = nullptr;
+    L.row_first = L.split = nullptr;
     L.tile_nnz = tile_nnz;
     L.ntiles = (int32_t)ceil_div(ctx->nnz, tile_nnz);
     L.nsplit = 0;
     const int nt = L.ntiles;
     CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_first, (size_t)std::max(nt, 1) * 4, s));
-    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_lo, (size_t)(nt + 1) * 4, s));
     count_launch(ctx, nt >= 2 ? 3 : 1);
-    tile_rows_kernel<<<(unsigned)ceil_div(nt + 1, 256), 256, 0, s>>>(L.seg, L.In, ctx->nnz, tile_nnz, nt, L.row_first,
-                                                                     L.row_lo);
+    tile_rows_kernel<<<(unsigned)ceil_div(std::max(nt, 1), 256), 256, 0, s>>>(L.seg, L.In, tile_nnz, nt, L.row_first);
     CPAPR_CUDA(ctx, cudaGetLastError());
     if (nt >= 2) {
         uint32_t *flag = nullptr, *dtot = nullptr;
@@ -548,8 +531,6 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
         CPAPR_CUDA(ctx, cudaMallocAsync(&ctx->carry, (size_t)need * ctx->esize, s));
         ctx->carry_elems = need;
     }
-    int64_t llneed = std::max(nt, 1);
-    (void)llneed;
     CPAPR_CUDA(ctx, cudaStreamSynchronize(s));
     return CPAPR_OK;
 }

@@ -3,10 +3,11 @@
 // Device layout of one context (all allocations owned by the context):
 //   per mode n (sorted by i_n once, at create):
 //     seg[n]      int32 [I_n + 1]    first sorted position of each row
+//     rid[n]      int32 [nnz_pad]    i_n of each nonzero in mode-n order (-1 past nnz)
 //     idx[n][k]   int32 [nnz_pad]    coordinate of the k-th other mode (k = 0..N-2,
 //                                    increasing mode number), in mode-n order
 //     val[n]      T     [nnz_pad]    counts in mode-n order (T = double or float)
-//     tile table  row_first[t], row_lo[t] and the list of rows that span tiles
+//     tile table  row_first[t] and the list of rows that span tiles
 //   model:  A[m] T [I_m x Rp], lambda double [Rp], B T [Imax x Rp],
 //           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration)
 //   scratch: carry T [2 x ntiles x Rp] (per-tile partial rows), reductions.
@@ -43,12 +44,12 @@ struct InnerState {
 struct ModeLayout {
     int32_t In = 0;
     int32_t *seg = nullptr;
+    int32_t *rid = nullptr;
     int32_t *idx[kMaxModes - 1] = {};
     void *val = nullptr;
     // tiles
     int32_t tile_nnz = 0, ntiles = 0, lanes = 1, reduction = CPAPR_REDUCE_SEGMENTED, threads = 256;
-    int32_t *row_first = nullptr;  // [ntiles]     row holding the tile's first nonzero
-    int32_t *row_lo = nullptr;     // [ntiles + 1] first row whose start lies in the tile; row_lo[ntiles] = In
+    int32_t *row_first = nullptr;  // [ntiles] row holding the tile's first nonzero
     int32_t nsplit = 0;
     int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
     int32_t nempty = 0;
@@ -160,6 +161,9 @@ cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
 cpapr_status launch_zero_empty(cpapr_ctx *ctx, int n, void *out);
 cpapr_status launch_empty_kkt(cpapr_ctx *ctx, int n, const void *B, InnerState *inner);
 bool phi_config_supported(int esize, int nm1, int rp, int lanes);
+// shared memory of a tile kernel launch, and the most a launch may use
+size_t phi_smem_for(int esize, int nm1, int tile, int rp, int lanes);
+constexpr size_t kMaxPhiSmem = 220 * 1024;
 
 // ---- MU kernels (mu.cu) -------------------------------------------------------
 cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner);

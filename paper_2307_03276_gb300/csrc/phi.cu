@@ -34,6 +34,12 @@ bool phi_config_supported(int esize, int nm1, int rp, int lanes) {
     return false;
 }
 
+// Shared memory of a tile kernel launch (staged streams + partial-row slots);
+// a tile size is usable when it stays within kMaxPhiSmem.
+size_t phi_smem_for(int esize, int nm1, int tile, int rp, int lanes) {
+    return phi_smem_bytes(tile, nm1, esize, esize == 8 ? 128 : 256, rp / lanes);
+}
+
 static cudaError_t dispatch(const cpapr_ctx *ctx, const PhiArgs &a, int rpl, int lanes, int op) {
     const int nm1 = ctx->N - 1;
     if (ctx->esize == 8) {
@@ -62,7 +68,7 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.In = L.In;
     a.nm1 = ctx->N - 1;
     a.atomic = L.reduction == CPAPR_REDUCE_ATOMIC ? 1 : 0;
-    a.seg = L.seg;
+    a.rid = L.rid;
     int k = 0;
     for (int m = 0; m < ctx->N; ++m) {
         if (m == n) continue;
@@ -74,13 +80,12 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.B = B;
     a.out = out;
     a.carry = ctx->carry;
-    a.row_first = L.row_first;
-    a.row_lo = L.row_lo;
     a.split = L.split;
     a.nsplit = L.nsplit;
     a.eps = ctx->opt.eps;
     a.inner = inner;
     a.llpart = ctx->llpart;
+    a.err = ctx->errflag + 3;
     return a;
 }
 

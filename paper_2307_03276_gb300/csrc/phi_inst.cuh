@@ -30,8 +30,7 @@ constexpr int unroll_for() {
 template <int RPL, int G, int OP>
 cudaError_t run(const PhiArgs &a, cudaStream_t s) {
     auto k = phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, unroll_for<RPL, G>()>;
-    size_t smem = 0;
-    if (OP != OP_LL && !a.atomic) smem = (size_t)2 * kThreads * RPL * sizeof(PHI_T) + (size_t)2 * (kThreads / G) * 4;
+    const size_t smem = phi_smem_bytes(a.T, a.nm1, (int)sizeof(PHI_T), kThreads, RPL);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -21,9 +21,12 @@
 //   3. a row cut by a tile boundary leaves a per-tile partial in the carry
 //      buffer; the fix-up kernel adds the partials of every such row in tile
 //      order (a fixed order, so results are bit-reproducible).
-// Rows whose first position lies in the tile but hold no nonzero are
-// written as zeros by that tile.  With reduction = ATOMIC, levels 2 and 3 are
-// replaced by atomic adds into a zeroed output.
+// Rows without nonzeros are never touched.  With reduction = ATOMIC, levels
+// 2 and 3 are replaced by atomic adds into a zeroed output.
+//
+// A tile's row ids, coordinates and values are first staged in shared
+// memory by bulk asynchronous copies, so that a batch reads them with a few
+// vector shared loads and only the factor-row gathers go to L1/L2.
 //
 // The KKT violation max_{i,r} |min(B, 1 - Phi)| of the MU loop is folded in:
 // whoever writes a final Phi row also reduces its violation, and one atomicMax
@@ -54,20 +57,19 @@ struct PhiArgs {
     int32_t In;
     int32_t nm1;     // number of gathered modes (N - 1)
     int32_t atomic;  // 1: partial rows are added with atomics into a zeroed output
-    const int32_t *seg;
+    const int32_t *rid;  // i_n of every nonzero in mode-n order
     const int32_t *idx[kMaxNm1];
     const void *val;
     const void *A[kMaxNm1];
     const void *B;
     void *out;
     void *carry;     // head partials [ntiles][Rp], then tail partials [ntiles][Rp]
-    const int32_t *row_first;
-    const int32_t *row_lo;
     const int32_t *split;
     int32_t nsplit;
     double eps;
     InnerState *inner;  // null for a one-off Phi (no KKT bookkeeping)
     double *llpart;     // OP_LL: one partial per tile
+    int32_t *err;       // set to 1 when a bounded wait gives up
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -157,17 +159,6 @@ __device__ __forceinline__ void publish_kkt(double v, InnerState *inner, double 
         for (int w = 0; w < THREADS / 32; ++w) m = fmax(m, sm[w]);
         if (m > 0.0) atomicMax(&inner->kkt[inner->l & 1], ordered_bits(m));
     }
-}
-
-__device__ __forceinline__ int32_t ub_seg(const int32_t *__restrict__ seg, int32_t lo, int32_t hi, int64_t p) {
-    while (lo < hi) {
-        int32_t mid = lo + ((hi - lo) >> 1);
-        if ((int64_t)__ldg(seg + mid) > p)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
 }
 
 template <typename T, int RPL>
@@ -274,23 +265,159 @@ __device__ __forceinline__ void store_row(T *__restrict__ base, const T (&src)[R
     }
 }
 
-// NM1: number of gathered modes (exact), or 0 for "runtime count up to kMaxNm1".
-// U: nonzeros whose gathers are issued together (memory-level parallelism).
-// Shared memory of one block: partial-row slots, 2 per group.
-template <typename T, int RPL, int THREADS>
-constexpr size_t phi_slot_bytes() {
-    return (size_t)2 * THREADS * RPL * sizeof(T) + (size_t)2 * THREADS * 4;
+// ---- staging of a tile's streams in shared memory ------------------------------
+//
+// A tile's row ids, its N-1 coordinate streams and its values are contiguous
+// runs in HBM.  One thread copies each run into shared memory with a bulk
+// asynchronous copy (cp.async.bulk; completion is counted in bytes on an
+// mbarrier) and the block waits on the barrier.  The wait is bounded in time:
+// if the copies have not landed after kStageWaitNs the block records the
+// failure in *a.err, waits once more for its copies and skips the tile (the
+// host then reports CPAPR_E_TIMEOUT).
+
+constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s
+
+// entries reserved per staged stream (a multiple of 4: 16-byte rows)
+__host__ __device__ constexpr int stage_cap(int T) { return (T + 3) & ~3; }
+
+// shared-memory bytes of a tile of T nonzeros: the staged streams (row ids,
+// N-1 coordinates, values) followed by the partial-row slots of the
+// segmented reduction (2 per group of lanes)
+__host__ __device__ constexpr size_t phi_smem_bytes(int T, int nm1, int esize, int threads, int rpl) {
+    return (size_t)stage_cap(T) * (size_t)(4 * (nm1 + 1) + esize) + (size_t)2 * threads * rpl * esize +
+           (size_t)2 * threads * 4;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_barrier_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool stage_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true once the phase with this parity has completed; false after
+// kStageWaitNs (or 2^26 polls) without completion
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity) {
+    if (stage_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (stage_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kStageWaitNs) break;
+    }
+    return false;
+}
+
+// U consecutive staged entries starting at a multiple of U (vector loads)
+template <int U>
+__device__ __forceinline__ void lds_u(const int32_t *p, int32_t (&d)[U]) {
+    if constexpr (U == 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(p);
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    } else if constexpr (U == 2) {
+        const int2 v = *reinterpret_cast<const int2 *>(p);
+        d[0] = v.x;
+        d[1] = v.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[u] = p[u];
+    }
+}
+template <int U>
+__device__ __forceinline__ void lds_u(const float *p, float (&d)[U]) {
+    if constexpr (U == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    } else if constexpr (U == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        d[0] = v.x;
+        d[1] = v.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[u] = p[u];
+    }
+}
+template <int U>
+__device__ __forceinline__ void lds_u(const double *p, double (&d)[U]) {
+    if constexpr (U % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < U / 2; ++h) {
+            const double2 v = reinterpret_cast<const double2 *>(p)[h];
+            d[2 * h] = v.x;
+            d[2 * h + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) d[u] = p[u];
+    }
+}
+
+// <B[row], pi> recomputed in FP64 from the stored factor values: the FP32
+// log-likelihood uses it where the FP32 product underflows (m < 2^-96).
+template <typename T, int RPL, int MAXK>
+__device__ __forceinline__ double dot_fp64(const PhiArgs &a, const int32_t (&ii)[MAXK], int32_t row, int col0, int nm1) {
+    const T *Bm = reinterpret_cast<const T *>(a.B) + (int64_t)row * a.Rp + col0;
+    double d = 0.0;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        double p = (double)__ldg(Bm + r);
+#pragma unroll
+        for (int k = 0; k < MAXK; ++k)
+            if (k < nm1) p *= (double)__ldg(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[k] * a.Rp + col0 + r);
+        d += p;
+    }
+    return d;
+}
+
+// NM1: number of gathered modes (exact), or 0 for "runtime count up to kMaxNm1".
+// U: nonzeros whose gathers are issued together (memory-level parallelism).
+//
 // One tile (t) of one tensor (a) by the whole block.  Every thread of the
-// block must call it with the same arguments.  smem_raw holds the slots
-// (phi_slot_bytes), red is NWARPS doubles.
+// block calls it with the same arguments.  smem_raw holds phi_smem_bytes();
+// red is NWARPS doubles; bar is the block's staging barrier (initialised) and
+// phase the parity of its next phase (flipped here whenever a tile is staged).
+// Returns false if the staging wait gave up (the caller stops).
 template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
-__device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red) {
+__device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red,
+                                              uint64_t *bar, uint32_t &phase) {
+    static_assert(U == 1 || U == 2 || U == 4, "batches of 1, 2 or 4 nonzeros");
     constexpr int NG = THREADS / G;
     constexpr int NWARPS = THREADS / 32;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
-    if (a.inner && a.inner->done) return;
+    if (a.inner && a.inner->done) return true;
     const int nm1 = NM1 > 0 ? NM1 : a.nm1;
     const int tid = threadIdx.x;
     const int g = tid / G, lane = tid % G;
@@ -298,27 +425,56 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
     const int Rp = RPL * G;
     const int64_t p0 = (int64_t)t * a.T;
     const int64_t p1 = min(p0 + (int64_t)a.T, a.nnz);
-    const int64_t vlen = ((int64_t)a.T + NG - 1) / NG;
-    const int64_t ga = min(p0 + (int64_t)g * vlen, p1);
-    const int64_t gb = min(ga + vlen, p1);
+    const int n = (int)(p1 - p0);
     const int col0 = lane * RPL;
     const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((wlane / G) * G));
 
-    T *slot_val = reinterpret_cast<T *>(smem_raw);                  // [2 * NG][Rp]
+    const int cap = stage_cap(a.T);
+    int32_t *s_rid = reinterpret_cast<int32_t *>(smem_raw);
+    int32_t *s_idx = s_rid + cap;  // [nm1][cap]
+    T *s_val = reinterpret_cast<T *>(s_idx + (int64_t)nm1 * cap);
+    T *slot_val = s_val + cap;                                                 // [2 * NG][Rp]
     int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
 
+    // the previous tile of a persistent block may still read the stage and the slots
+    __syncthreads();
+    if (tid == 0) {
+        // order this block's earlier generic accesses of the stage before the async writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t b4 = (uint32_t)(((int64_t)n * 4 + 15) & ~(int64_t)15);
+        const uint32_t bv = (uint32_t)(((int64_t)n * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
+        stage_expect(bar, b4 * (uint32_t)(nm1 + 1) + bv);
+        stage_copy(s_rid, a.rid + p0, b4, bar);
+        for (int k = 0; k < nm1; ++k) stage_copy(s_idx + (int64_t)k * cap, a.idx[k] + p0, b4, bar);
+        stage_copy(s_val, reinterpret_cast<const T *>(a.val) + p0, bv, bar);
+    }
     const bool segmented = (OP != OP_LL) && !a.atomic;
-    if (segmented) {
-        __syncthreads();  // the previous tile of a persistent block may still read the slots
+    if (segmented)
         for (int s = tid; s < 2 * NG; s += THREADS) slot_row[s] = -1;
-        __syncthreads();
+    const bool landed = stage_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!landed)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        if (!landed) stage_wait(bar, phase ^ 1u);  // let the copies finish before the block moves on
+        return false;
     }
 
-    const int32_t *__restrict__ seg = a.seg;
-    const T *__restrict__ val = reinterpret_cast<const T *>(a.val);
     const T *__restrict__ Bm = reinterpret_cast<const T *>(a.B);
     T *__restrict__ out = reinterpret_cast<T *>(a.out);
     const T eps = (T)a.eps;
+
+    // Contiguous run [la, lb) of the tile for this group.  Runs start on
+    // multiples of U (vector loads of a batch).  With one lane per group an
+    // FP32 run length is made odd so that the 32 threads of a warp read 32
+    // banks; FP64 keeps equal runs (its FP64 pipe hides the bank conflicts,
+    // a longer run would not be hidden).
+    int vlen = (a.T + NG - 1) / NG;
+    if (G == 1) {
+        if (sizeof(T) == 4) vlen |= 1;
+    } else {
+        vlen = (vlen + U - 1) / U * U;
+    }
+    const int la = min(g * vlen, n), lb = min(la + vlen, n);
 
     T kkt = T(0);
     double ll = 0.0;
@@ -329,15 +485,16 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
     // B rows held in registers (reused along a row), except for wide FP64
     // lanes, whose registers go to the Khatri-Rao row and the accumulator:
     // there the dot reads the B row through L1 for every nonzero
-    constexpr bool BREG = !(sizeof(T) == 8 && (RPL >= 16 || U >= 4));
+    constexpr bool BREG = (OP != OP_MTTKRP) && !(sizeof(T) == 8 && (RPL >= 16 || U >= 4));
     constexpr int BR = BREG ? RPL : 1;
 
-    if (ga < gb) {
-        int32_t row = ub_seg(seg, a.row_first[t], a.row_lo[t + 1], ga) - 1;
-        int64_t rend = __ldg(seg + row + 1);
-        int64_t rbeg = __ldg(seg + row);
-        int32_t cur = row;
-        int64_t cbeg = rbeg, cend = rend;
+    if (la < lb) {
+        // does the row at la begin before the run, the row at lb - 1 go on after it?
+        auto rid_at = [&](int64_t p) -> int32_t { return (p >= p0 && p < p1) ? s_rid[p - p0] : __ldg(a.rid + p); };
+        const bool head_open = p0 + la > 0 && rid_at(p0 + la - 1) == s_rid[la];
+        const bool tail_open = p0 + lb < a.nnz && rid_at(p0 + lb) == s_rid[lb - 1];
+        int32_t cur = s_rid[la];
+        bool first_run = true;
         // Run accumulation (segmented, plain FMA).  FP32 interleaves two
         // accumulators so that each sums at most half of a run; the row sums
         // across groups and tiles are the compensated ones.
@@ -347,77 +504,87 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
         for (int h = 0; h < NACC; ++h)
 #pragma unroll
             for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
-        T brow[BR];  // B row of `cur` (loaded once per row, not per nonzero)
-        int32_t brow_row = -1;
-#pragma unroll
-        for (int r = 0; r < BR; ++r) brow[r] = T(0);
+        T brow[BR];  // B row of `brow_row` (loaded once per row, not per nonzero)
+        int32_t brow_row = cur;
+        if constexpr (BREG) load_row<T, BR>(Bm + (int64_t)cur * Rp + col0, brow);
 
-        auto flush = [&](int32_t frow, int64_t fbeg, int64_t fend, const T(&bq)[BR]) {
+        auto flush = [&](int32_t frow, bool first, bool last) {
             T v[RPL];
 #pragma unroll
             for (int r = 0; r < RPL; ++r) v[r] = NACC == 2 ? acc[0][r] + acc[NACC - 1][r] : acc[0][r];
-            if (fbeg >= ga && fend <= gb) {
+            const bool before = first && head_open, after = last && tail_open;
+            if (!before && !after) {
                 store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
                 if (OP == OP_PHI) {
                     if constexpr (BREG) {
+                        if (frow == brow_row) {
 #pragma unroll
-                        for (int r = 0; r < RPL; ++r) kkt = tmax(kkt, viol_t(bq[r], v[r]));
-                    } else {
-#pragma unroll
-                        for (int r = 0; r < RPL; ++r)
-                            kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)frow * Rp + col0 + r), v[r]));
+                            for (int r = 0; r < RPL; ++r) kkt = tmax(kkt, viol_t(brow[r], v[r]));
+                            return;
+                        }
                     }
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r)
+                        kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)frow * Rp + col0 + r), v[r]));
                 }
             } else if (a.atomic) {
 #pragma unroll
                 for (int r = 0; r < RPL; ++r) atomicAdd(out + (int64_t)frow * Rp + col0 + r, v[r]);
             } else {
-                const int s = fbeg < ga ? 2 * g : 2 * g + 1;
+                const int s = before ? 2 * g : 2 * g + 1;
                 if (lane == 0) slot_row[s] = frow;
                 store_row<T, RPL>(slot_val + (int64_t)s * Rp + col0, v);
             }
         };
 
-        for (int64_t q = ga; q < gb; q += U) {
+        for (int q = la; q < lb; q += U) {
+            int32_t rr[U];
             int32_t ii[U][MAXK];
             T xx[U];
-            int32_t rr[U];
-            int64_t rb[U], re[U];
+            if constexpr (G == 1) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t qq = min(q + u, gb - 1);
-                xx[u] = __ldg(val + qq);
+                for (int u = 0; u < U; ++u) {
+                    const int qq = min(q + u, lb - 1);
+                    rr[u] = s_rid[qq];
+                    xx[u] = s_val[qq];
 #pragma unroll
-                for (int k = 0; k < MAXK; ++k)
-                    if (k < nm1) ii[u][k] = __ldg(a.idx[k] + qq);
-                if (qq >= rend) {  // next row; jump over empty rows by bisection
-                    ++row;
-                    rbeg = rend;
-                    rend = __ldg(seg + row + 1);
-                    if (qq >= rend) {
-                        row = ub_seg(seg, row + 1, a.row_lo[t + 1], qq) - 1;
-                        rbeg = __ldg(seg + row);
-                        rend = __ldg(seg + row + 1);
+                    for (int k = 0; k < MAXK; ++k)
+                        if (k < nm1) ii[u][k] = s_idx[(int64_t)k * cap + qq];
+                }
+            } else {
+                lds_u<U>(s_rid + q, rr);
+                lds_u<U>(s_val + q, xx);
+#pragma unroll
+                for (int k = 0; k < MAXK; ++k) {
+                    if (k < nm1) {
+                        int32_t tmp[U];
+                        lds_u<U>(s_idx + (int64_t)k * cap + q, tmp);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) ii[u][k] = tmp[u];
                     }
                 }
-                rr[u] = row;
-                rb[u] = rbeg;
-                re[u] = rend;
+                if (q + U > lb) {  // ragged end of the run: repeat its first entry (never accumulated)
+#pragma unroll
+                    for (int u = 1; u < U; ++u) {
+                        if (q + u >= lb) {
+                            rr[u] = rr[0];
+                            xx[u] = xx[0];
+#pragma unroll
+                            for (int k = 0; k < MAXK; ++k) ii[u][k] = ii[0][k];
+                        }
+                    }
+                }
             }
-            // gathers of the batch: Khatri-Rao rows, and a B row only where the row changes
+            // every nonzero of the batch in the current row (the common case)
+            const bool fast = q + U <= lb && rr[U - 1] == cur;
+
             T pi[U][RPL];
-            T bb[U][BR];
-            bool newb[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 load_row<T, RPL>(reinterpret_cast<const T *>(a.A[0]) + (int64_t)ii[u][0] * Rp + col0, pi[u]);
 #pragma unroll
                 for (int k = 1; k < MAXK; ++k)
                     if (k < nm1) mul_row<T, RPL>(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[u][k] * Rp + col0, pi[u]);
-                if (OP != OP_MTTKRP && BREG) {
-                    newb[u] = rr[u] != (u == 0 ? brow_row : rr[u > 0 ? u - 1 : 0]);
-                    if (newb[u]) load_row<T, BR>(Bm + (int64_t)rr[u] * Rp + col0, bb[u]);
-                }
             }
             T v[U];
             if (OP == OP_MTTKRP) {
@@ -425,28 +592,28 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
                 for (int u = 0; u < U; ++u) v[u] = xx[u];
             } else {
                 T s[U];
+                if (BREG && fast) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if constexpr (BREG) {
-                        if (!newb[u]) {
-#pragma unroll
-                            for (int r = 0; r < BR; ++r) bb[u][r] = u == 0 ? brow[r] : bb[u > 0 ? u - 1 : 0][r];
-                        }
-                        if constexpr (BR == RPL) s[u] = dot_regs<T, RPL>(bb[u], pi[u]);
-                    } else {
-                        s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
+                    for (int u = 0; u < U; ++u) {
+                        if constexpr (BREG) s[u] = dot_regs<T, RPL>(brow, pi[u]);
                     }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
                 }
                 if constexpr (G == 1) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         if (OP == OP_PHI) {
                             v[u] = phi_divide(xx[u], tmax(s[u], eps));
-                        } else if (q + u < gb) {  // OP_LL: x log(m), m = <lambda o A^(n)[i_n], pi>
-                            if constexpr (sizeof(T) == 8)
+                        } else if (q + u < lb) {  // OP_LL: x log(m), m = <lambda o A^(n)[i_n], pi>
+                            if constexpr (sizeof(T) == 8) {
                                 ll += (double)xx[u] * log((double)s[u]);
-                            else
-                                ll += (double)xx[u] * (double)logf((float)s[u]);
+                            } else {
+                                double m = (double)s[u];
+                                if (s[u] < 0x1p-96f) m = dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1);
+                                ll += (double)xx[u] * log(m);
+                            }
                         }
                     }
                 } else {
@@ -459,43 +626,68 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
                         const T vm = phi_divide(xm, tmax(tot, eps));
 #pragma unroll
                         for (int u = 0; u < U; ++u) v[u] = __shfl_sync(gmask, vm, gbase + u * LPU);
-                    } else if (q + u_mine < gb && (lane % LPU) == 0) {
-                        if constexpr (sizeof(T) == 8)
-                            ll += (double)xm * log((double)tot);
-                        else
-                            ll += (double)xm * (double)logf((float)tot);
+                    } else {
+                        double m = (double)tot;
+                        if constexpr (sizeof(T) == 4) {
+                            // FP32 underflow of the model value: redo the group's
+                            // dots in FP64 (rare; all lanes of the group join)
+                            if (__any_sync(gmask, tot < 0x1p-96f)) {
+                                double d[U];
+#pragma unroll
+                                for (int u = 0; u < U; ++u) d[u] = dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1);
+#pragma unroll
+                                for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+                                    for (int u = 0; u < U; ++u) d[u] += __shfl_xor_sync(gmask, d[u], o);
+                                if (tot < 0x1p-96f) {
+                                    m = d[0];
+#pragma unroll
+                                    for (int u = 1; u < U; ++u)
+                                        if (u_mine == u) m = d[u];
+                                }
+                            }
+                        }
+                        if (q + u_mine < lb && (lane % LPU) == 0) ll += (double)xm * log(m);
                     }
                 }
             }
-            if (OP != OP_LL) {
+            if (fast) {
+                if (OP != OP_LL) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (q + u < gb) {
-                        if (rr[u] != cur) {
-                            if (u == 0)
-                                flush(cur, cbeg, cend, brow);
-                            else
-                                flush(cur, cbeg, cend, bb[u > 0 ? u - 1 : 0]);
-                            cur = rr[u];
-                            cbeg = rb[u];
-                            cend = re[u];
-#pragma unroll
-                            for (int h = 0; h < NACC; ++h)
-#pragma unroll
-                                for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
-                        }
+                    for (int u = 0; u < U; ++u)
 #pragma unroll
                         for (int r = 0; r < RPL; ++r) acc[u % NACC][r] = fma(v[u], pi[u][r], acc[u % NACC][r]);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (q + u < lb) {
+                        if (rr[u] != cur) {
+                            if (OP != OP_LL) {
+                                flush(cur, first_run, false);
+#pragma unroll
+                                for (int h = 0; h < NACC; ++h)
+#pragma unroll
+                                    for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
+                            }
+                            first_run = false;
+                            cur = rr[u];
+                        }
+                        if (OP != OP_LL) {
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r) acc[u % NACC][r] = fma(v[u], pi[u][r], acc[u % NACC][r]);
+                        }
+                    }
+                }
+                if constexpr (BREG) {
+                    if (cur != brow_row) {
+                        load_row<T, BR>(Bm + (int64_t)cur * Rp + col0, brow);
+                        brow_row = cur;
                     }
                 }
             }
-            if (OP != OP_MTTKRP && BREG) {
-#pragma unroll
-                for (int r = 0; r < BR; ++r) brow[r] = bb[U - 1][r];
-                brow_row = rr[U - 1];
-            }
         }
-        if (OP != OP_LL) flush(cur, cbeg, cend, brow);
+        if (OP != OP_LL) flush(cur, first_run, true);
     }
 
     if (OP == OP_LL) {
@@ -508,7 +700,7 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
             for (int w = 0; w < NWARPS; ++w) s += red[w];
             a.llpart[t] = s;
         }
-        return;
+        return true;
     }
 
     if (segmented) {
@@ -518,6 +710,7 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
         // of the following groups while they hold the same row
         T *carry_head = reinterpret_cast<T *>(a.carry) + (int64_t)t * Rp;
         T *carry_tail = reinterpret_cast<T *>(a.carry) + ((int64_t)a.ntiles + t) * Rp;
+        const int32_t next_row = p1 < a.nnz ? __ldg(a.rid + p1) : -1;  // row at the next tile's start
         for (int s = warp; s < 2 * NG; s += NWARPS) {
             if (!(s == 0 || (s & 1))) continue;
             const int32_t crow = slot_row[s];
@@ -525,7 +718,7 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
             const int gs = s >> 1;
             int gend = gs + 1;
             while (gend < NG && slot_row[2 * gend] == crow) ++gend;
-            const bool complete = s != 0 && (int64_t)__ldg(seg + crow + 1) <= p1;
+            const bool complete = s != 0 && crow != next_row;
             for (int c = wlane; c < Rp; c += 32) {
                 KSum<T> sum;
                 sum.zero();
@@ -548,14 +741,19 @@ __device__ __forceinline__ void phi_tile_body(const PhiArgs &a, const int t, uns
         // update those B rows are zero).
     }
     if (OP == OP_PHI && a.inner && !a.atomic) publish_kkt<THREADS>(kkt, a.inner, red);
+    return true;
 }
 
 // One block per tile of one tensor.
 template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
 __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[THREADS / 32];
-    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red);
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) stage_barrier_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
 }
 
 // Adds the per-tile partials of every row that spans tiles, in tile order,

@@ -253,6 +253,7 @@ cpapr_status autotune(cpapr_ctx *ctx) {
         for (int lanes = 1; lanes <= 32; lanes <<= 1) {
             if (!phi_config_supported((int)ctx->esize, ctx->N - 1, Rp, lanes)) continue;
             for (int tile : tiles) {
+                if (phi_smem_for((int)ctx->esize, ctx->N - 1, tile, Rp, lanes) > kMaxPhiSmem) continue;
                 for (int red = CPAPR_REDUCE_ATOMIC; red <= CPAPR_REDUCE_SEGMENTED; ++red) {
                     CPAPR_TRY(configure_mode(ctx, n, lanes, tile, red));
                     CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, nullptr));

@@ -85,7 +85,7 @@ def test_phi_fp64_matches_oracle(name, reduction):
 
 
 @pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s64"])
-@pytest.mark.parametrize("tile", [64, 320, 8192])
+@pytest.mark.parametrize("tile", [64, 320, 4096])
 def test_phi_fp64_tile_sizes(name, tile):
     """Small tiles cut many rows across tiles and groups (fix-up path), large ones few."""
     T = case(name)
@@ -382,6 +382,24 @@ def test_ranks_not_power_of_two(rank):
             for n in range(3):
                 want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
                 assert max_rel(t.phi(n), want) <= tol, (rank, prec, n)
+
+
+def test_tile_size_limits():
+    """A tile's staged streams must fit in shared memory and start on 16-byte
+    boundaries: the largest 3-way FP64 tile works, larger or odd sizes are
+    argument errors, not faults."""
+    T = case("c2s")
+    lam, fs = model_for(T, 9)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=8192) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= 1e-12
+    for name, tile in (("c2s", 66), ("c2s", 16384), ("c5s64", 8192)):
+        T = case(name)
+        with pytest.raises(cpapr.CpaprError) as e:
+            cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=tile)
+        assert e.value.status == 1, (name, tile)
 
 
 def test_invalid_inputs_are_errors_not_faults():
