@@ -266,8 +266,8 @@ cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info);
 
 /*
  * Per-kernel device time recorded while opt.profile = 1 (CUDA events on the
- * context's stream).  kind 0 = Phi tile kernel, 1 = Phi boundary fix-up,
- * 2 = MU update, 3 = normalisation, 4 = S and B, 5 = log-likelihood,
+ * context's stream).  kind 0 = Phi tile kernel (rows that span tiles are
+ * finished inside it), 1 = reserved (always 0 launches), 2 = MU update, 3 = normalisation, 4 = S and B, 5 = log-likelihood,
  * 6 = MTTKRP.  Returns the launch count and the summed milliseconds since
  * the last reset; reset = 1 clears the counters after reading.
  */

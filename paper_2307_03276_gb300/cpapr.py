@@ -20,7 +20,7 @@ MAX_MODES = 8
 
 CPAPR_FP64, CPAPR_FP32 = 0, 1
 CPAPR_REDUCE_AUTO, CPAPR_REDUCE_ATOMIC, CPAPR_REDUCE_SEGMENTED = 0, 1, 2
-K_PHI, K_FIXUP, K_UPDATE, K_NORM, K_SB, K_LL, K_MTTKRP = range(7)
+K_PHI, K_RESERVED, K_UPDATE, K_NORM, K_SB, K_LL, K_MTTKRP = range(7)
 
 STATUS = {0: "CPAPR_OK", 1: "CPAPR_E_ARG", 2: "CPAPR_E_RANGE", 3: "CPAPR_E_VALUE", 4: "CPAPR_E_NOMEM",
           5: "CPAPR_E_CUDA", 6: "CPAPR_E_TIMEOUT", 7: "CPAPR_E_STATE"}

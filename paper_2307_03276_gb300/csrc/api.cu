@@ -239,6 +239,8 @@ void cpapr_destroy(cpapr_ctx *ctx) {
         ModeLayout &L = ctx->mode[n];
         if (L.row_first) cudaFree(L.row_first);
         if (L.split) cudaFree(L.split);
+        if (L.tsplit) cudaFree(L.tsplit);
+        if (L.splitcnt) cudaFree(L.splitcnt);
         if (ctx->graph_exec[n]) cudaGraphExecDestroy(ctx->graph_exec[n]);
     }
     if (ctx->carry) cudaFree(ctx->carry);
@@ -469,6 +471,12 @@ static cpapr_status check_waits(cpapr_ctx *ctx) {
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (!f) return CPAPR_OK;
     CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag + 3, 0, 4, ctx->stream));
+    // tiles that gave up never counted their partials: clear the counters
+    for (int n = 0; n < ctx->N; ++n)
+        if (ctx->mode[n].splitcnt)
+            CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->mode[n].splitcnt, 0,
+                                            (size_t)std::max(ctx->mode[n].nsplit, 1) * 4, ctx->stream));
+    CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return fail(ctx, CPAPR_E_TIMEOUT, "a device-side staging wait gave up; the results of this call are incomplete");
 }
 

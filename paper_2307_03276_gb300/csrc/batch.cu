@@ -6,13 +6,12 @@
 //                        blocks pull (tensor, tile) items from a counter;
 //                        each item runs the tile body instantiated for its
 //                        tensor's rank class)
-//   batch_fixup_kernel   rows cut by tile boundaries           (split rows)
 //   batch_update_kernel  B_t <- B_t * Phi_t unless tensor t passed its KKT
 //                        check; per-tensor bookkeeping by the last block of
 //                        the tensor, loop condition by the last block overall
 //   batch_colsum/scale   lambda_t <- e^T B_t, A_t <- B_t Lambda_t^-1
 // The inner loop is one CUDA graph with a conditional WHILE node whose body
-// is {phi, fixup, update}; it runs while any tensor still iterates.  Tensors
+// is {phi, update}; it runs while any tensor still iterates.  Tensors
 // that converged are masked on the device (their kernels return at once).
 // Every reduction keeps a fixed order (results are reproducible run to run);
 // a tensor's result equals solving it alone up to the order of the column
@@ -136,17 +135,6 @@ __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) bat
             __threadfence();
         }
     }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) batch_fixup_kernel(const BatchTensor *__restrict__ desc,
-                                                          const int2 *__restrict__ items) {
-    __shared__ T sm_s[256];
-    __shared__ T sm_c[256];
-    __shared__ double red[8];
-    const int2 w = items[blockIdx.x];
-    const PhiArgs a = desc[w.x].a;
-    phi_fixup_body<T, OP_PHI>(a, w.y, sm_s, sm_c, red);
 }
 
 // flags[2t] = skip (converged or finished), flags[2t+1] = apply the shift S
@@ -322,8 +310,8 @@ __global__ void gather_states_kernel(InnerState *const *src, int n, InnerState *
 // ---------------------------------------------------------------------------
 struct ModePlan {
     BatchTensor *desc = nullptr;
-    int2 *tiles = nullptr, *splits = nullptr, *chunks = nullptr, *echunks = nullptr;
-    int ntiles = 0, nsplits = 0, nchunks = 0, nechunks = 0;
+    int2 *tiles = nullptr, *chunks = nullptr, *echunks = nullptr;
+    int ntiles = 0, nchunks = 0, nechunks = 0;
     cudaGraphExec_t exec = nullptr;
     int body_kernels = 0;
     size_t smem = 0;  // dynamic shared memory of the Phi launch (largest tile of the batch)
@@ -386,10 +374,6 @@ cpapr_status enqueue_inner_body(cpapr_ctx *c0, Plan &P, int n, double tol, int m
     ModePlan &mp = P.modes[n];
     cudaStream_t s = c0->stream;
     if (mp.ntiles > 0) CPAPR_CUDA(c0, launch_phi_batch<T>(mp, c0->N - 1, grid, P.ctl, s));
-    if (mp.nsplits > 0) {
-        batch_fixup_kernel<T><<<mp.nsplits, 256, 0, s>>>(mp.desc, mp.splits);
-        CPAPR_CUDA(c0, cudaGetLastError());
-    }
     batch_update_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.chunk_count, P.ctl, tol, max_inner, h,
                                                       use_cond);
     CPAPR_CUDA(c0, cudaGetLastError());
@@ -431,7 +415,7 @@ cpapr_status build_graph(cpapr_ctx *c0, Plan &P, int n, double tol, int max_inne
     e = cudaGraphInstantiate(&mp.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c0, e, "cudaGraphInstantiate(batch)");
-    mp.body_kernels = 1 + (mp.nsplits > 0 ? 1 : 0) + 1;
+    mp.body_kernels = 2;
     return CPAPR_OK;
 }
 
@@ -527,7 +511,6 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         ModePlan &mp = P.modes[n];
         std::vector<BatchTensor> desc(count);
         std::vector<int2> tiles, chunks, echunks;
-        std::vector<int2> splits;
         for (int i = 0; i < count; ++i) {
             cpapr_ctx *c = ctxs[i];
             const ModeLayout &L = c->mode[n];
@@ -554,6 +537,8 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.out = c->Phi[n];
             a.carry = c->carry;
             a.split = L.split;
+            a.tsplit = L.tsplit;
+            a.splitcnt = L.splitcnt;
             a.nsplit = L.nsplit;
             a.eps = c->opt.eps;
             a.inner = c->inner + n;
@@ -572,7 +557,6 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             d.erows = L.erows;
             d.nempty = c->nnz > 0 ? L.nempty : 0;
             for (int t = 0; t < (c->nnz > 0 ? L.ntiles : 0); ++t) tiles.push_back(make_int2(i, t));
-            for (int t = 0; t < (c->nnz > 0 ? L.nsplit : 0); ++t) splits.push_back(make_int2(i, t));
             for (int t = 0; t < d.nchunks; ++t) chunks.push_back(make_int2(i, t));
             for (int t = 0; t < (int)ceil_div(d.nempty * c->Rp, kEmptyChunk); ++t) echunks.push_back(make_int2(i, t));
         }
@@ -588,12 +572,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             mp.smem = phi_smem_bytes(maxtile, N - 1, (int)sizeof(T), batch_threads<T>(), maxrpl);
             smem_max = std::max(smem_max, mp.smem);
         }
-        mp.nsplits = (int)splits.size();
         mp.nchunks = (int)chunks.size();
         mp.nechunks = (int)echunks.size();
         BT_CUDA(dalloc((void **)&mp.desc, desc.size() * sizeof(BatchTensor)));
         BT_CUDA(dalloc((void **)&mp.tiles, tiles.size() * sizeof(int2)));
-        BT_CUDA(dalloc((void **)&mp.splits, splits.size() * sizeof(int2)));
         BT_CUDA(dalloc((void **)&mp.chunks, chunks.size() * sizeof(int2)));
         BT_CUDA(dalloc((void **)&mp.echunks, echunks.size() * sizeof(int2)));
         if (!echunks.empty())
@@ -601,8 +583,6 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         BT_CUDA(cudaMemcpy(mp.desc, desc.data(), desc.size() * sizeof(BatchTensor), cudaMemcpyHostToDevice));
         if (!tiles.empty())
             BT_CUDA(cudaMemcpy(mp.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
-        if (!splits.empty())
-            BT_CUDA(cudaMemcpy(mp.splits, splits.data(), splits.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
     }
     if (smem_max > kMaxPhiSmem) {

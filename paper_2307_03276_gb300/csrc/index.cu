@@ -491,12 +491,32 @@ __global__ void split_write_kernel(const int32_t *__restrict__ seg, const int32_
     }
 }
 
+// tsplit[2t] = split whose row holds tile t's head partial (the row began in
+// an earlier tile), tsplit[2t+1] = split whose first tile is t (tile t's tail
+// partial); -1 where there is none.  pos = exclusive scan of the split-start
+// flags, total = their sum: the splits started at or before tile u number
+// incl(u) = pos[u + 1] (total for the last tile).
+__global__ void tile_split_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ row_first, int32_t T,
+                                  int32_t ntiles, const uint32_t *__restrict__ pos, const uint32_t *__restrict__ total,
+                                  int32_t *__restrict__ tsplit) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    auto incl = [&](int u) -> int32_t { return (int32_t)(u + 1 < ntiles ? pos[u + 1] : *total); };
+    int32_t head = -1, tail = -1;
+    if (t >= 1 && (int64_t)seg[row_first[t]] < (int64_t)t * T) head = incl(t) - 1;
+    if (t + 1 < ntiles && incl(t + 1) - (int32_t)pos[t + 1] == 1) tail = (int32_t)pos[t + 1];
+    tsplit[2 * t] = head;
+    tsplit[2 * t + 1] = tail;
+}
+
 cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     ModeLayout &L = ctx->mode[n];
     cudaStream_t s = ctx->stream;
     if (L.row_first) cudaFreeAsync(L.row_first, s);
     if (L.split) cudaFreeAsync(L.split, s);
-    L.row_first = L.split = nullptr;
+    if (L.tsplit) cudaFreeAsync(L.tsplit, s);
+    if (L.splitcnt) cudaFreeAsync(L.splitcnt, s);
+    L.row_first = L.split = L.tsplit = L.splitcnt = nullptr;
     L.tile_nnz = tile_nnz;
     L.ntiles = (int32_t)ceil_div(ctx->nnz, tile_nnz);
     L.nsplit = 0;
@@ -519,10 +539,19 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
         CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, (size_t)std::max<int>(L.nsplit, 1) * 12, s));
         split_write_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag, L.split);
         CPAPR_CUDA(ctx, cudaGetLastError());
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.tsplit, (size_t)nt * 8, s));
+        tile_split_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag, dtot,
+                                                                      L.tsplit);
+        count_launch(ctx);
+        CPAPR_CUDA(ctx, cudaGetLastError());
         CPAPR_CUDA(ctx, cudaFreeAsync(flag, s));
     } else {
         CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, 12, s));
+        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.tsplit, (size_t)std::max(nt, 1) * 8, s));
+        CPAPR_CUDA(ctx, cudaMemsetAsync(L.tsplit, 0xff, (size_t)std::max(nt, 1) * 8, s));
     }
+    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.splitcnt, (size_t)std::max(L.nsplit, 1) * 4, s));
+    CPAPR_CUDA(ctx, cudaMemsetAsync(L.splitcnt, 0, (size_t)std::max(L.nsplit, 1) * 4, s));
     // the carry buffer holds two partial rows per tile
     int64_t need = (int64_t)2 * std::max(nt, 1) * ctx->Rp;
     if (need > ctx->carry_elems) {

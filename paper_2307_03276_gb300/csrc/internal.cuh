@@ -7,7 +7,8 @@
 //     idx[n][k]   int32 [nnz_pad]    coordinate of the k-th other mode (k = 0..N-2,
 //                                    increasing mode number), in mode-n order
 //     val[n]      T     [nnz_pad]    counts in mode-n order (T = double or float)
-//     tile table  row_first[t] and the list of rows that span tiles
+//     tile table  row_first[t], the rows that span tiles, each tile's
+//                 split of its head and tail partial, per-split counters
 //   model:  A[m] T [I_m x Rp], lambda double [Rp], B T [Imax x Rp],
 //           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration)
 //   scratch: carry T [2 x ntiles x Rp] (per-tile partial rows), reductions.
@@ -27,7 +28,7 @@ namespace cpapr {
 
 constexpr int kMaxModes = CPAPR_MAX_MODES;
 
-enum KernelKind { K_PHI = 0, K_FIXUP = 1, K_UPDATE = 2, K_NORM = 3, K_SB = 4, K_LL = 5, K_MTTKRP = 6, K_NKINDS = 7 };
+enum KernelKind { K_PHI = 0, K_RESERVED = 1, K_UPDATE = 2, K_NORM = 3, K_SB = 4, K_LL = 5, K_MTTKRP = 6, K_NKINDS = 7 };
 
 // Device-side state of one mode's inner loop (written by the kernels only).
 struct InnerState {
@@ -52,6 +53,8 @@ struct ModeLayout {
     int32_t *row_first = nullptr;  // [ntiles] row holding the tile's first nonzero
     int32_t nsplit = 0;
     int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
+    int32_t *tsplit = nullptr;     // [2 * ntiles] split of each tile's head / tail partial, or -1
+    int32_t *splitcnt = nullptr;   // [nsplit] partial counters of the tile kernel (zero between launches)
     int32_t nempty = 0;
     int32_t *erows = nullptr;      // [nempty] rows without nonzeros, increasing
 };

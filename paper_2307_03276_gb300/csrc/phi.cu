@@ -81,22 +81,14 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.out = out;
     a.carry = ctx->carry;
     a.split = L.split;
+    a.tsplit = L.tsplit;
+    a.splitcnt = L.splitcnt;
     a.nsplit = L.nsplit;
     a.eps = ctx->opt.eps;
     a.inner = inner;
     a.llpart = ctx->llpart;
     a.err = ctx->errflag + 3;
     return a;
-}
-
-template <typename T>
-static cudaError_t run_fixup(const PhiArgs &a, int op, cudaStream_t s) {
-    if (a.nsplit <= 0) return cudaSuccess;
-    if (op == OP_PHI)
-        phi_fixup_kernel<T, OP_PHI><<<a.nsplit, 256, 0, s>>>(a);
-    else
-        phi_fixup_kernel<T, OP_MTTKRP><<<a.nsplit, 256, 0, s>>>(a);
-    return cudaGetLastError();
 }
 
 template <typename T>
@@ -160,12 +152,6 @@ cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *ou
         if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "phi tile kernel");
     }
-    if (ctx->nnz > 0 && !atomic && L.nsplit > 0) {
-        ProfScope ps(ctx, K_FIXUP);
-        count_launch(ctx);
-        cudaError_t e = ctx->esize == 8 ? run_fixup<double>(a, op, ctx->stream) : run_fixup<float>(a, op, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "phi fix-up kernel");
-    }
     if (op == OP_PHI && inner && (atomic || ctx->nnz == 0)) {
         count_launch(ctx);
         cudaError_t e = ctx->esize == 8
@@ -190,11 +176,6 @@ cpapr_status launch_phi_given_carry(cpapr_ctx *ctx, int n, const void *B, void *
     count_launch(ctx);
     if (e == cudaErrorInvalidValue) return fail(ctx, CPAPR_E_ARG, "no kernel for this rank / lane choice");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "phi tile kernel");
-    if (L.nsplit > 0) {
-        e = ctx->esize == 8 ? run_fixup<double>(a, OP_PHI, ctx->stream) : run_fixup<float>(a, OP_PHI, ctx->stream);
-        count_launch(ctx);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "phi fix-up kernel");
-    }
     return CPAPR_OK;
 }
 

@@ -19,8 +19,9 @@
 //      memory; after a barrier the block adds each chain of partials in group
 //      order and stores the row if it ends inside the tile;
 //   3. a row cut by a tile boundary leaves a per-tile partial in the carry
-//      buffer; the fix-up kernel adds the partials of every such row in tile
-//      order (a fixed order, so results are bit-reproducible).
+//      buffer and counts it on the row's counter; the tile whose partial
+//      arrives last adds all of them in tile order (a fixed order, so results
+//      are bit-reproducible) and stores the row.
 // Rows without nonzeros are never touched.  With reduction = ATOMIC, levels
 // 2 and 3 are replaced by atomic adds into a zeroed output.
 //
@@ -64,7 +65,9 @@ struct PhiArgs {
     const void *B;
     void *out;
     void *carry;     // head partials [ntiles][Rp], then tail partials [ntiles][Rp]
-    const int32_t *split;
+    const int32_t *split;   // [nsplit][3]: rows that span tiles (row, first tile, last tile)
+    const int32_t *tsplit;  // [ntiles][2]: split of the tile's head partial, of its tail partial (-1: none)
+    int32_t *splitcnt;      // [nsplit]: partials arrived in this launch (zero between launches)
     int32_t nsplit;
     double eps;
     InnerState *inner;  // null for a one-off Phi (no KKT bookkeeping)
@@ -285,7 +288,7 @@ __host__ __device__ constexpr int stage_cap(int T) { return (T + 3) & ~3; }
 // segmented reduction (2 per group of lanes)
 __host__ __device__ constexpr size_t phi_smem_bytes(int T, int nm1, int esize, int threads, int rpl) {
     return (size_t)stage_cap(T) * (size_t)(4 * (nm1 + 1) + esize) + (size_t)2 * threads * rpl * esize +
-           (size_t)2 * threads * 4;
+           (size_t)2 * threads * 4 + 16;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -435,6 +438,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     T *s_val = reinterpret_cast<T *>(s_idx + (int64_t)nm1 * cap);
     T *slot_val = s_val + cap;                                                 // [2 * NG][Rp]
     int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
+    int32_t *slot_fin = slot_row + 2 * NG;  // [2]: rows spanning tiles this block finishes
 
     // the previous tile of a persistent block may still read the stage and the slots
     __syncthreads();
@@ -449,8 +453,10 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         stage_copy(s_val, reinterpret_cast<const T *>(a.val) + p0, bv, bar);
     }
     const bool segmented = (OP != OP_LL) && !a.atomic;
-    if (segmented)
+    if (segmented) {
         for (int s = tid; s < 2 * NG; s += THREADS) slot_row[s] = -1;
+        if (tid < 2) slot_fin[tid] = -1;
+    }
     const bool landed = stage_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!landed)) {
@@ -609,10 +615,10 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                         } else if (q + u < lb) {  // OP_LL: x log(m), m = <lambda o A^(n)[i_n], pi>
                             if constexpr (sizeof(T) == 8) {
                                 ll += (double)xx[u] * log((double)s[u]);
+                            } else if (s[u] < 0x1p-96f) {
+                                ll += (double)xx[u] * log(dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1));
                             } else {
-                                double m = (double)s[u];
-                                if (s[u] < 0x1p-96f) m = dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1);
-                                ll += (double)xx[u] * log(m);
+                                ll += (double)xx[u] * (double)logf((float)s[u]);
                             }
                         }
                     }
@@ -626,28 +632,30 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                         const T vm = phi_divide(xm, tmax(tot, eps));
 #pragma unroll
                         for (int u = 0; u < U; ++u) v[u] = __shfl_sync(gmask, vm, gbase + u * LPU);
+                    } else if constexpr (sizeof(T) == 8) {
+                        if (q + u_mine < lb && (lane % LPU) == 0) ll += (double)xm * log((double)tot);
                     } else {
-                        double m = (double)tot;
-                        if constexpr (sizeof(T) == 4) {
-                            // FP32 underflow of the model value: redo the group's
-                            // dots in FP64 (rare; all lanes of the group join)
-                            if (__any_sync(gmask, tot < 0x1p-96f)) {
-                                double d[U];
+                        // FP32 log of the model value (FP64 logs would load the
+                        // FP64 pipe); where the FP32 value underflows, the
+                        // group's dots are redone in FP64 (all its lanes join)
+                        double lm = (double)logf((float)tot);
+                        if (__any_sync(gmask, tot < 0x1p-96f)) {
+                            double d[U];
 #pragma unroll
-                                for (int u = 0; u < U; ++u) d[u] = dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1);
+                            for (int u = 0; u < U; ++u) d[u] = dot_fp64<T, RPL, MAXK>(a, ii[u], rr[u], col0, nm1);
 #pragma unroll
-                                for (int o = G / 2; o > 0; o >>= 1)
+                            for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
-                                    for (int u = 0; u < U; ++u) d[u] += __shfl_xor_sync(gmask, d[u], o);
-                                if (tot < 0x1p-96f) {
-                                    m = d[0];
+                                for (int u = 0; u < U; ++u) d[u] += __shfl_xor_sync(gmask, d[u], o);
+                            if (tot < 0x1p-96f) {
+                                double m = d[0];
 #pragma unroll
-                                    for (int u = 1; u < U; ++u)
-                                        if (u_mine == u) m = d[u];
-                                }
+                                for (int u = 1; u < U; ++u)
+                                    if (u_mine == u) m = d[u];
+                                lm = log(m);
                             }
                         }
-                        if (q + u_mine < lb && (lane % LPU) == 0) ll += (double)xm * log(m);
+                        if (q + u_mine < lb && (lane % LPU) == 0) ll += (double)xm * lm;
                     }
                 }
             }
@@ -708,8 +716,9 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         // chains of partials: slot 0 (a row that began before the tile) and
         // every tail slot start a chain that continues through the head slots
         // of the following groups while they hold the same row
-        T *carry_head = reinterpret_cast<T *>(a.carry) + (int64_t)t * Rp;
-        T *carry_tail = reinterpret_cast<T *>(a.carry) + ((int64_t)a.ntiles + t) * Rp;
+        T *carry = reinterpret_cast<T *>(a.carry);
+        T *carry_head = carry + (int64_t)t * Rp;
+        T *carry_tail = carry + ((int64_t)a.ntiles + t) * Rp;
         const int32_t next_row = p1 < a.nnz ? __ldg(a.rid + p1) : -1;  // row at the next tile's start
         for (int s = warp; s < 2 * NG; s += NWARPS) {
             if (!(s == 0 || (s & 1))) continue;
@@ -734,6 +743,69 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                     carry_tail[c] = v;
                 }
             }
+            if (s == 0 || !complete) {
+                // a partial of a row that spans tiles: publish it, and if it
+                // is the row's last partial to arrive this block adds them up
+                __threadfence();
+                __syncwarp();
+                if (wlane == 0) {
+                    const int32_t si = __ldg(a.tsplit + 2 * t + (s == 0 ? 0 : 1));
+                    if (si >= 0 && si < a.nsplit) {  // always, by construction of the table
+                        const int32_t parts = __ldg(a.split + 3 * si + 2) - __ldg(a.split + 3 * si + 1) + 1;
+                        if (atomicAdd(a.splitcnt + si, 1) == parts - 1) slot_fin[s == 0 ? 0 : 1] = si;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // Rows that span tiles, finished by the tile whose partial came last:
+        // the partials (tail of the first tile, heads of the others) are
+        // added in tile order, so the result does not depend on which tile
+        // finishes.  Columns are split into chunks of tiles across the block
+        // and the chunk sums combined in chunk order.
+#pragma unroll 1
+        for (int f = 0; f < 2; ++f) {
+            const int32_t si = slot_fin[f];
+            if (si < 0) continue;
+            __threadfence();
+            const int32_t crow = __ldg(a.split + 3 * si + 0);
+            const int32_t t0 = __ldg(a.split + 3 * si + 1);
+            const int npart = __ldg(a.split + 3 * si + 2) - t0 + 1;
+            auto part = [&](int k, int c) -> T {
+                const int64_t off = k == 0 ? ((int64_t)a.ntiles + t0) * Rp : (int64_t)(t0 + k) * Rp;
+                return __ldcg(carry + off + c);
+            };
+            if (Rp < THREADS) {
+                const int nch = THREADS / Rp, c = tid % Rp, chunk = tid / Rp;
+                KSum<T> sum;
+                sum.zero();
+                for (int k = chunk; k < npart; k += nch) sum.add(part(k, c));
+                slot_val[tid] = sum.s;
+                slot_val[THREADS + tid] = sum.c;
+                __syncthreads();
+                if (tid < Rp) {
+                    KSum<T> tot;
+                    tot.zero();
+                    for (int k = 0; k < nch; ++k) {
+                        tot.add(slot_val[k * Rp + c]);
+                        tot.add(-slot_val[THREADS + k * Rp + c]);
+                    }
+                    const T v = tot.value();
+                    out[(int64_t)crow * Rp + c] = v;
+                    if (OP == OP_PHI) kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)crow * Rp + c), v));
+                }
+                __syncthreads();
+            } else {
+                for (int c = tid; c < Rp; c += THREADS) {
+                    KSum<T> sum;
+                    sum.zero();
+                    for (int k = 0; k < npart; ++k) sum.add(part(k, c));
+                    const T v = sum.value();
+                    out[(int64_t)crow * Rp + c] = v;
+                    if (OP == OP_PHI) kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)crow * Rp + c), v));
+                }
+            }
+            if (tid == 0) a.splitcnt[si] = 0;  // ready for the next launch
         }
         // Rows without nonzeros are never written here: their Phi row is zero
         // in a buffer that starts zeroed, and their KKT term min(B, 1) is
@@ -754,57 +826,6 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     __syncthreads();
     uint32_t phase = 0;
     phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
-}
-
-// Adds the per-tile partials of every row that spans tiles, in tile order,
-// and stores the row (plus its KKT violation).  One block per such row.
-// Body for split row `si` of tensor `a`; 256 threads, all calling it.
-template <typename T, int OP>
-__device__ __forceinline__ void phi_fixup_body(const PhiArgs &a, const int si, T *sm_s, T *sm_c, double *red) {
-    if (a.inner && a.inner->done) return;
-    const int Rp = a.Rp;
-    const int32_t row = a.split[3 * si + 0];
-    const int32_t t0 = a.split[3 * si + 1];
-    const int32_t t1 = a.split[3 * si + 2];
-    const int c = threadIdx.x % Rp;
-    const int chunk = threadIdx.x / Rp;
-    const int nchunks = blockDim.x / Rp;
-    const T *carry = reinterpret_cast<const T *>(a.carry);
-    const int npart = t1 - t0 + 1;
-    KSum<T> sum;
-    sum.zero();
-    if (chunk < nchunks) {
-        for (int k = chunk; k < npart; k += nchunks) {
-            const int64_t off = k == 0 ? ((int64_t)a.ntiles + t0) * Rp : (int64_t)(t0 + k) * Rp;
-            sum.add(carry[off + c]);
-        }
-    }
-    sm_s[threadIdx.x] = sum.s;
-    sm_c[threadIdx.x] = sum.c;
-    __syncthreads();
-    double kkt = 0.0;
-    if (threadIdx.x < Rp) {
-        KSum<T> tot;
-        tot.zero();
-        for (int k = 0; k < nchunks; ++k) {
-            tot.add(sm_s[k * Rp + c]);
-            tot.add(-sm_c[k * Rp + c]);
-        }
-        const T v = tot.value();
-        reinterpret_cast<T *>(a.out)[(int64_t)row * Rp + c] = v;
-        if (OP == OP_PHI)
-            kkt = (double)viol_t(reinterpret_cast<const T *>(a.B)[(int64_t)row * Rp + c], v);
-    }
-    if (OP == OP_PHI && a.inner) publish_kkt<256>(kkt, a.inner, red);
-    __syncthreads();  // sm_s / sm_c are reused by the next split row of a persistent block
-}
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(256) phi_fixup_kernel(const PhiArgs a) {
-    __shared__ T sm_s[256];
-    __shared__ T sm_c[256];
-    __shared__ double red[8];
-    phi_fixup_body<T, OP>(a, blockIdx.x, sm_s, sm_c, red);
 }
 
 // KKT term of the rows without nonzeros, |min(B, 1 - 0)|, published into
