@@ -148,7 +148,8 @@ static int next_pow2(int v) {
 // one lane per nonzero up to 16 ranks (no shuffle adds on the scarce FP64
 // pipe), 8 ranks per lane above with batches of four nonzeros; FP32: 16-byte
 // vectors of 4 ranks per lane up to 32 ranks, 8 ranks per lane above, and the
-// largest tile whose shared-memory stage leaves room for three blocks per SM.
+// largest tile whose shared-memory stage leaves room for the blocks per SM
+// the tile kernel is built for (four with one float4 per lane, else three).
 static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
     const int Rp = ctx->Rp;
     int g;
@@ -160,10 +161,12 @@ static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile,
     if (ctx->esize == 8) {
         *tile = Rp <= 16 ? 2048 : 1024;
     } else {
-        // the largest tile whose shared-memory stage still lets three blocks share an SM
+        // the largest tile whose shared-memory stage still lets the kernel's
+        // resident blocks (4 with one float4 per lane, else 3) share an SM
+        const size_t per_block = (Rp / g <= 4 ? 227 / 4 : 227 / 3) * 1024 - 1024;
         *tile = 1024;
         for (int t : {4096, 2048})
-            if (phi_smem_for(4, ctx->N - 1, t, Rp, g) <= 74 * 1024) {
+            if (phi_smem_for(4, ctx->N - 1, t, Rp, g) <= per_block) {
                 *tile = t;
                 break;
             }

@@ -83,7 +83,9 @@ __host__ __device__ constexpr int batch_unroll() {
 }
 
 template <typename T> __host__ __device__ constexpr int batch_threads() { return sizeof(T) == 8 ? 128 : 256; }
-template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 2; }
+// resident blocks per SM the registers are held to (the FP32 classes all
+// keep one float4 per lane, like the single-tensor kernel's four-block case)
+template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 4; }
 
 template <typename T, int NM1, int K>
 __device__ __forceinline__ bool run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red, uint64_t *bar,

@@ -27,9 +27,8 @@ constexpr int unroll_for() {
     return G >= 4 ? 4 : 2;
 }
 
-template <int RPL, int G, int OP>
-cudaError_t run(const PhiArgs &a, cudaStream_t s) {
-    auto k = phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, unroll_for<RPL, G>()>;
+template <int RPL, typename K>
+cudaError_t launch(K k, const PhiArgs &a, cudaStream_t s) {
     const size_t smem = phi_smem_bytes(a.T, a.nm1, (int)sizeof(PHI_T), kThreads, RPL);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -37,6 +36,15 @@ cudaError_t run(const PhiArgs &a, cudaStream_t s) {
     }
     if (a.ntiles > 0) k<<<a.ntiles, kThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int RPL, int G, int OP>
+cudaError_t run(const PhiArgs &a, cudaStream_t s) {
+    constexpr int U = unroll_for<RPL, G>();
+    if constexpr (phi_occ4<PHI_T, RPL>())
+        return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U>, a, s);
+    else
+        return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U>, a, s);
 }
 }  // namespace
 

@@ -107,10 +107,26 @@ template <typename T> __device__ __forceinline__ T viol_t(T b, T phi) {
     return m < T(0) ? -m : m;
 }
 
-// x / max(s, eps): IEEE division in FP64; the fast reciprocal-based division
-// in FP32 (within 2 ulp, far inside the FP32 path's 1e-5 tolerance).
-__device__ __forceinline__ double phi_divide(double x, double m) { return x / m; }
-__device__ __forceinline__ float phi_divide(float x, float m) { return __fdividef(x, m); }
+// x / max(s, eps) of Algorithm 2.
+// FP64: s >= 0, so the maximum is taken on the bit patterns (integer ALU,
+// not the FP64 pipe).  The quotient is x * r1 with r1 the correctly rounded
+// FP32 reciprocal of m (relative error below 2^-23 together with the
+// rounding of m to float) refined by one Newton-Raphson step for 1/m,
+// r1 = r0 + r0 (1 - m r0), which squares the relative error (below 2^-46)
+// up to FP64 rounding: three FP64 operations instead of the longer IEEE
+// division on GB300's narrow FP64 pipe, far inside the 1e-12 parity bound.
+// Where m does not fit a normal float the IEEE division runs.
+// FP32: the fast reciprocal-based division (within 2 ulp, far inside the
+// FP32 path's 1e-5 tolerance).
+__device__ __forceinline__ double phi_divide(double x, double s, double eps) {
+    const double m = __longlong_as_double(max(__double_as_longlong(s), __double_as_longlong(eps)));
+    const float mf = __double2float_rn(m);
+    if (__float_as_uint(mf) - 0x00800000u >= 0x7e000000u) return x / m;  // zero, subnormal, >= 2^125, inf, NaN
+    const double r0 = (double)__frcp_rn(mf);
+    const double r1 = fma(r0, fma(-m, r0, 1.0), r0);
+    return x * r1;
+}
+__device__ __forceinline__ float phi_divide(float x, float s, float eps) { return __fdividef(x, s > eps ? s : eps); }
 
 // On entry each of the G lanes of a group holds U partial dot products (its
 // RPL ranks) of the group's U nonzeros.  A reduce-scatter halves the set at
@@ -611,7 +627,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         if (OP == OP_PHI) {
-                            v[u] = phi_divide(xx[u], tmax(s[u], eps));
+                            v[u] = phi_divide(xx[u], s[u], eps);
                         } else if (q + u < lb) {  // OP_LL: x log(m), m = <lambda o A^(n)[i_n], pi>
                             if constexpr (sizeof(T) == 8) {
                                 ll += (double)xx[u] * log((double)s[u]);
@@ -629,7 +645,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                     for (int u = 1; u < U; ++u)
                         if (u_mine == u) xm = xx[u];
                     if (OP == OP_PHI) {
-                        const T vm = phi_divide(xm, tmax(tot, eps));
+                        const T vm = phi_divide(xm, tot, eps);
 #pragma unroll
                         for (int u = 0; u < U; ++u) v[u] = __shfl_sync(gmask, vm, gbase + u * LPU);
                     } else if constexpr (sizeof(T) == 8) {
@@ -826,6 +842,26 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     __syncthreads();
     uint32_t phase = 0;
     phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
+}
+
+// The same with registers held to four resident blocks per SM (64 per
+// thread at 256 threads): measured on GB300 the better trade for FP32 with
+// one float4 per lane, where more warps hide more gather latency.
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+__global__ void __launch_bounds__(THREADS, 4) phi_tile_kernel_occ4(const PhiArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[THREADS / 32];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) stage_barrier_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
+}
+
+// FP32 with one float4 per lane runs at four blocks per SM
+template <typename T, int RPL>
+__host__ __device__ constexpr bool phi_occ4() {
+    return sizeof(T) == 4 && RPL <= 4;
 }
 
 // KKT term of the rows without nonzeros, |min(B, 1 - 0)|, published into
