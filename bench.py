@@ -315,7 +315,7 @@ def batched_run(cp, torch, precision, steps, warmup, count=64):
     return out
 
 
-KERNEL_NAMES = ("phi_tile", "reserved", "mu_update", "normalise", "s_and_b", "loglik", "mttkrp")
+KERNEL_NAMES = ("phi_tile", "pi_build", "mu_update", "normalise", "s_and_b", "loglik", "mttkrp")
 
 
 def kernel_breakdown(stats, steps):

@@ -52,6 +52,7 @@ typedef enum {
 
 enum { CPAPR_FP64 = 0, CPAPR_FP32 = 1 };
 enum { CPAPR_REDUCE_AUTO = 0, CPAPR_REDUCE_ATOMIC = 1, CPAPR_REDUCE_SEGMENTED = 2 };
+enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
 
 /*
  * Options.  Fill with cpapr_default_options() and change what you need.
@@ -76,11 +77,22 @@ enum { CPAPR_REDUCE_AUTO = 0, CPAPR_REDUCE_ATOMIC = 1, CPAPR_REDUCE_SEGMENTED = 
  *  rank_lanes lanes that share one nonzero (1..32, power of two); 0 = automatic.
  *  use_graph  1 = run each mode's inner loop as a CUDA graph with a device-side
  *             early exit (default), 0 = plain stream launches.
- *  autotune   1 = time candidate (tile_nnz, rank_lanes, reduction) choices on
- *             the tensor when it is created and keep the fastest per mode;
- *             0 = use the built-in heuristic (default).
+ *  autotune   1 = time candidate (tile_nnz, rank_lanes, reduction, pi_mode)
+ *             choices on the tensor when it is created and keep the fastest
+ *             per mode; 0 = use the built-in heuristic (default).
  *  profile    1 = record CUDA events around every Phi launch so that
  *             cpapr_kernel_stats() can report per-kernel device time.
+ *  pi_mode    the Khatri-Rao rows Pi of Algorithm 3.  CPAPR_PI_FUSED: formed
+ *             per nonzero inside every Phi evaluation from the factor rows.
+ *             CPAPR_PI_MATERIALISED: built once per mode and outer iteration
+ *             (the factors of the other modes do not change within a mode's
+ *             inner loop) into a buffer of nnz x R values of the working
+ *             precision, which every Phi of the inner loop streams; results
+ *             are identical to the fused form.  CPAPR_PI_AUTO (default):
+ *             materialised in FP64 with three or more modes when the buffer
+ *             takes at most half of the free device memory, else fused.
+ *             MTTKRP, the log-likelihood and the batched solver always form
+ *             the rows in place.
  */
 typedef struct {
     int32_t precision;
@@ -95,7 +107,8 @@ typedef struct {
     int32_t use_graph;
     int32_t autotune;
     int32_t profile;
-    int32_t reserved[5];
+    int32_t pi_mode;
+    int32_t reserved[4];
 } cpapr_options;
 
 void cpapr_default_options(cpapr_options *opt);
@@ -258,6 +271,7 @@ typedef struct {
     int32_t reduction[CPAPR_MAX_MODES];   /* chosen per mode */
     int32_t ntiles[CPAPR_MAX_MODES];
     int32_t nsplit[CPAPR_MAX_MODES];      /* rows that span more than one tile */
+    int32_t pi_mode[CPAPR_MAX_MODES];     /* CPAPR_PI_FUSED or CPAPR_PI_MATERIALISED, per mode */
     int64_t device_bytes;  /* device memory held by the context */
     int64_t kernel_launches; /* kernels this context has launched (graph replays counted per kernel) */
 } cpapr_info;
@@ -267,7 +281,7 @@ cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info);
 /*
  * Per-kernel device time recorded while opt.profile = 1 (CUDA events on the
  * context's stream).  kind 0 = Phi tile kernel (rows that span tiles are
- * finished inside it), 1 = reserved (always 0 launches), 2 = MU update, 3 = normalisation, 4 = S and B, 5 = log-likelihood,
+ * finished inside it), 1 = materialised Khatri-Rao rows, 2 = MU update, 3 = normalisation, 4 = S and B, 5 = log-likelihood,
  * 6 = MTTKRP.  Returns the launch count and the summed milliseconds since
  * the last reset; reset = 1 clears the counters after reading.
  */

@@ -20,7 +20,8 @@ MAX_MODES = 8
 
 CPAPR_FP64, CPAPR_FP32 = 0, 1
 CPAPR_REDUCE_AUTO, CPAPR_REDUCE_ATOMIC, CPAPR_REDUCE_SEGMENTED = 0, 1, 2
-K_PHI, K_RESERVED, K_UPDATE, K_NORM, K_SB, K_LL, K_MTTKRP = range(7)
+CPAPR_PI_AUTO, CPAPR_PI_FUSED, CPAPR_PI_MATERIALISED = 0, 1, 2
+K_PHI, K_PI, K_UPDATE, K_NORM, K_SB, K_LL, K_MTTKRP = range(7)
 
 STATUS = {0: "CPAPR_OK", 1: "CPAPR_E_ARG", 2: "CPAPR_E_RANGE", 3: "CPAPR_E_VALUE", 4: "CPAPR_E_NOMEM",
           5: "CPAPR_E_CUDA", 6: "CPAPR_E_TIMEOUT", 7: "CPAPR_E_STATE"}
@@ -40,7 +41,7 @@ class Options(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("kappa_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile_nnz", ctypes.c_int32), ("rank_lanes", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("pi_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Result(ctypes.Structure):
@@ -57,7 +58,8 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("nnz", ctypes.c_int64), ("dims", ctypes.c_int64 * MAX_MODES),
                 ("tile_nnz", ctypes.c_int32 * MAX_MODES), ("rank_lanes", ctypes.c_int32 * MAX_MODES),
                 ("reduction", ctypes.c_int32 * MAX_MODES), ("ntiles", ctypes.c_int32 * MAX_MODES),
-                ("nsplit", ctypes.c_int32 * MAX_MODES), ("device_bytes", ctypes.c_int64),
+                ("nsplit", ctypes.c_int32 * MAX_MODES), ("pi_mode", ctypes.c_int32 * MAX_MODES),
+                ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64)]
 
 

@@ -202,6 +202,41 @@ cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int redu
     return CPAPR_OK;
 }
 
+// Materialised Khatri-Rao rows: one buffer of nnz_pad x Rp elements shared by
+// the modes (a mode's rows are rebuilt at the start of its inner loop).
+cpapr_status configure_pi(cpapr_ctx *ctx, int n, int on) {
+    ModeLayout &L = ctx->mode[n];
+    if (on && ctx->N >= 2 && ctx->nnz > 0 && !ctx->pibuf) {
+        void *p = nullptr;
+        CPAPR_TRY(dev_alloc(ctx, &p, (size_t)ctx->nnz_pad * ctx->Rp * ctx->esize));
+        ctx->pibuf = p;
+    }
+    L.pi = on && ctx->pibuf ? 1 : 0;
+    if (ctx->graph_exec[n]) {
+        cudaGraphExecDestroy(ctx->graph_exec[n]);
+        ctx->graph_exec[n] = nullptr;
+    }
+    return CPAPR_OK;
+}
+
+// The materialised rows are worth a buffer when there are Khatri-Rao
+// products to save (three or more modes) and it takes at most half of the
+// free device memory (or is already there).
+int pi_fits(const cpapr_ctx *ctx) {
+    if (ctx->N < 3 || ctx->nnz == 0) return 0;
+    if (ctx->pibuf) return 1;
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (double)ctx->nnz_pad * ctx->Rp * ctx->esize <= 0.5 * (double)freeb ? 1 : 0;
+}
+
+// Automatic choice: materialise in FP64, where the products cost time on the
+// narrow FP64 pipe; the FP32 form gathers and multiplies in place.
+int pi_auto(const cpapr_ctx *ctx) { return ctx->esize == 8 ? pi_fits(ctx) : 0; }
+
 cpapr_status autotune(cpapr_ctx *ctx);
 
 }  // namespace cpapr
@@ -357,6 +392,7 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
         if (o.tile_nnz) tile = o.tile_nnz;
         if (o.reduction) red = o.reduction;
         CR_TRY(configure_mode(ctx, n, lanes, tile, red));
+        CR_TRY(configure_pi(ctx, n, o.pi_mode == CPAPR_PI_MATERIALISED ? 1 : o.pi_mode == CPAPR_PI_FUSED ? 0 : pi_auto(ctx)));
     }
     if (o.autotune) CR_TRY(autotune(ctx));
     e = cudaStreamSynchronize(ctx->stream);
@@ -501,6 +537,7 @@ cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *ou
     }
     // Phi[mode] holds the previous iteration's Phi that S reads: compute into
     // the separate output buffer instead.
+    CPAPR_TRY(launch_pi_build(ctx, mode));
     CPAPR_TRY(launch_phi(ctx, mode, OP_PHI, ctx->B, ctx->outbuf, nullptr));
     CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -570,6 +607,7 @@ cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info) {
         info->reduction[m] = ctx->mode[m].reduction;
         info->ntiles[m] = ctx->mode[m].ntiles;
         info->nsplit[m] = ctx->mode[m].nsplit;
+        info->pi_mode[m] = ctx->mode[m].pi ? CPAPR_PI_MATERIALISED : CPAPR_PI_FUSED;
     }
     info->device_bytes = ctx->device_bytes;
     info->kernel_launches = ctx->launches;

@@ -28,7 +28,7 @@ namespace cpapr {
 
 constexpr int kMaxModes = CPAPR_MAX_MODES;
 
-enum KernelKind { K_PHI = 0, K_RESERVED = 1, K_UPDATE = 2, K_NORM = 3, K_SB = 4, K_LL = 5, K_MTTKRP = 6, K_NKINDS = 7 };
+enum KernelKind { K_PHI = 0, K_PI = 1, K_UPDATE = 2, K_NORM = 3, K_SB = 4, K_LL = 5, K_MTTKRP = 6, K_NKINDS = 7 };
 
 // Device-side state of one mode's inner loop (written by the kernels only).
 struct InnerState {
@@ -55,6 +55,7 @@ struct ModeLayout {
     int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
     int32_t *tsplit = nullptr;     // [2 * ntiles] split of each tile's head / tail partial, or -1
     int32_t *splitcnt = nullptr;   // [nsplit] partial counters of the tile kernel (zero between launches)
+    int32_t pi = 0;                // 1: Phi streams the materialised Khatri-Rao rows (built per outer iteration)
     int32_t nempty = 0;
     int32_t *erows = nullptr;      // [nempty] rows without nonzeros, increasing
 };
@@ -85,6 +86,7 @@ struct cpapr_ctx {
     double *stage = nullptr;  // FP64 staging for I/O (Imax x Rp)
     void *carry = nullptr;
     int64_t carry_elems = 0;
+    void *pibuf = nullptr;  // materialised Khatri-Rao rows of the current mode [nnz_pad x Rp]
     double *colpart = nullptr;   // column-sum partials [kColParts x Rp]
     double *colsum = nullptr;    // per-mode column sums [N x Rp]
     double *llpart = nullptr;    // per-tile log-likelihood partials
@@ -157,6 +159,12 @@ enum PhiOp { OP_PHI = 0, OP_MTTKRP = 1, OP_LL = 2 };
 // B: I_n x Rp of the working type (ignored for MTTKRP).  inner: state whose
 // done flag / kkt slot the kernels use (may be null for a one-off Phi).
 cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner);
+// builds the materialised Khatri-Rao rows of mode n (a no-op unless the mode uses them)
+cpapr_status launch_pi_build(cpapr_ctx *ctx, int n);
+// selects the materialised (on = 1) or fused (0) Khatri-Rao rows for mode n
+cpapr_status configure_pi(cpapr_ctx *ctx, int n, int on);
+int pi_auto(const cpapr_ctx *ctx);
+int pi_fits(const cpapr_ctx *ctx);
 // Sum of x log(m) over nonzeros, into llpart then *dst (device double).
 cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
 // Rows of mode n without nonzeros: zero them in `out`; add their KKT term

@@ -95,6 +95,7 @@ extern "C" cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const do
             CPAPR_TRY(launch_scale_b(ctx, mode, ctx->B));
         // the per-tile partials land in the fixed scratch; every slot the
         // fix-up reads is written earlier in this call, so nothing is cleared
+        CPAPR_TRY(launch_pi_build(ctx, mode));
         CPAPR_TRY(launch_phi_given_carry(ctx, mode, ctx->B, ctx->outbuf, scratch));
         CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
     }

@@ -133,10 +133,36 @@ cpapr_status launch_empty_kkt(cpapr_ctx *ctx, int n, const void *B, InnerState *
     return CPAPR_OK;
 }
 
+template <typename T>
+static cudaError_t run_pi_build(const PhiArgs &a, T *pi, cudaStream_t s) {
+    const int64_t total = a.nnz * (a.Rp / Vec16<T>::n);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 152 * 16));
+    switch (a.nm1) {
+        case 2: pi_build_kernel<T, 2><<<grid, 256, 0, s>>>(a, pi); break;
+        case 3: pi_build_kernel<T, 3><<<grid, 256, 0, s>>>(a, pi); break;
+        case 4: pi_build_kernel<T, 4><<<grid, 256, 0, s>>>(a, pi); break;
+        default: pi_build_kernel<T, 0><<<grid, 256, 0, s>>>(a, pi); break;
+    }
+    return cudaGetLastError();
+}
+
+cpapr_status launch_pi_build(cpapr_ctx *ctx, int n) {
+    if (!ctx->mode[n].pi || ctx->nnz == 0) return CPAPR_OK;
+    if (!ctx->pibuf) return fail(ctx, CPAPR_E_STATE, "materialised Pi selected without its buffer");
+    PhiArgs a = make_args(ctx, n, nullptr, nullptr, nullptr);
+    ProfScope ps(ctx, K_PI);
+    count_launch(ctx);
+    const cudaError_t e = ctx->esize == 8 ? run_pi_build<double>(a, (double *)ctx->pibuf, ctx->stream)
+                                          : run_pi_build<float>(a, (float *)ctx->pibuf, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Pi build kernel");
+    return CPAPR_OK;
+}
+
 cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner) {
     ModeLayout &L = ctx->mode[n];
     const int64_t nel = (int64_t)L.In * ctx->Rp;
     PhiArgs a = make_args(ctx, n, B, out, inner);
+    if (op == OP_PHI && L.pi) a.pi = ctx->pibuf;
     const bool atomic = a.atomic && op != OP_LL;
     if (ctx->nnz == 0 || atomic) {
         CPAPR_CUDA(ctx, cudaMemsetAsync(out, 0, (size_t)nel * ctx->esize, ctx->stream));
@@ -170,6 +196,7 @@ cpapr_status launch_phi_given_carry(cpapr_ctx *ctx, int n, const void *B, void *
     PhiArgs a = make_args(ctx, n, B, out, nullptr);
     a.atomic = 0;
     a.carry = carry;
+    if (L.pi) a.pi = ctx->pibuf;
     if (ctx->nnz == 0) return fail(ctx, CPAPR_E_ARG, "empty tensor");
     CPAPR_TRY(launch_zero_empty(ctx, n, out));
     cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_PHI);

@@ -29,7 +29,7 @@ constexpr int unroll_for() {
 
 template <int RPL, typename K>
 cudaError_t launch(K k, const PhiArgs &a, cudaStream_t s) {
-    const size_t smem = phi_smem_bytes(a.T, a.nm1, (int)sizeof(PHI_T), kThreads, RPL);
+    const size_t smem = phi_smem_bytes(a.T, a.pi ? 0 : a.nm1, (int)sizeof(PHI_T), kThreads, RPL);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -38,23 +38,25 @@ cudaError_t launch(K k, const PhiArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int RPL, int G, int OP>
+template <int RPL, int G, int OP, bool PI>
 cudaError_t run(const PhiArgs &a, cudaStream_t s) {
     constexpr int U = unroll_for<RPL, G>();
     if constexpr (phi_occ4<PHI_T, RPL>())
-        return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U>, a, s);
+        return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s);
     else
-        return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U>, a, s);
+        return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s);
 }
 }  // namespace
 
 // Returns cudaErrorInvalidValue when (rpl, lanes) has no instantiation.
+// Phi reads the materialised Khatri-Rao rows when a.pi is set.
 cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s) {
-#define CPAPR_CASE(R_, G_)                                                   \
-    if (rpl == R_ && lanes == G_) {                                          \
-        if (op == OP_PHI) return run<R_, G_, OP_PHI>(a, s);                  \
-        if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP>(a, s);            \
-        return run<R_, G_, OP_LL>(a, s);                                     \
+#define CPAPR_CASE(R_, G_)                                                               \
+    if (rpl == R_ && lanes == G_) {                                                      \
+        if (op == OP_PHI)                                                                \
+            return a.pi ? run<R_, G_, OP_PHI, true>(a, s) : run<R_, G_, OP_PHI, false>(a, s); \
+        if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP, false>(a, s);                 \
+        return run<R_, G_, OP_LL, false>(a, s);                                          \
     }
 #if PHI_IS_DOUBLE
     CPAPR_CASE(2, 1)

@@ -73,6 +73,7 @@ struct PhiArgs {
     InnerState *inner;  // null for a one-off Phi (no KKT bookkeeping)
     double *llpart;     // OP_LL: one partial per tile
     int32_t *err;       // set to 1 when a bounded wait gives up
+    const void *pi;     // materialised Khatri-Rao rows [nnz][Rp] in mode-n order, or null
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -188,6 +189,28 @@ __device__ __forceinline__ void load_row(const T *__restrict__ base, T (&dst)[RP
 #pragma unroll
     for (int v = 0; v < RPL / VN; ++v) {
         V x = __ldg(p + v);
+        if constexpr (VN == 4) {
+            dst[4 * v + 0] = x.x;
+            dst[4 * v + 1] = x.y;
+            dst[4 * v + 2] = x.z;
+            dst[4 * v + 3] = x.w;
+        } else {
+            dst[2 * v + 0] = x.x;
+            dst[2 * v + 1] = x.y;
+        }
+    }
+}
+
+// load_row for data read once (evict-first: the materialised Pi streams
+// through L2 without displacing the factor rows)
+template <typename T, int RPL>
+__device__ __forceinline__ void load_row_stream(const T *__restrict__ base, T (&dst)[RPL]) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    const V *p = reinterpret_cast<const V *>(base);
+#pragma unroll
+    for (int v = 0; v < RPL / VN; ++v) {
+        V x = __ldcs(p + v);
         if constexpr (VN == 4) {
             dst[4 * v + 0] = x.x;
             dst[4 * v + 1] = x.y;
@@ -429,15 +452,19 @@ __device__ __forceinline__ double dot_fp64(const PhiArgs &a, const int32_t (&ii)
 // red is NWARPS doubles; bar is the block's staging barrier (initialised) and
 // phase the parity of its next phase (flipped here whenever a tile is staged).
 // Returns false if the staging wait gave up (the caller stops).
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+// PI: the Khatri-Rao rows are read from the materialised Pi (a.pi, one row
+// per nonzero in mode-n order) instead of being formed from the factors; the
+// stage then holds only the row ids and the values.
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI = false>
 __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red,
                                               uint64_t *bar, uint32_t &phase) {
     static_assert(U == 1 || U == 2 || U == 4, "batches of 1, 2 or 4 nonzeros");
+    static_assert(!PI || OP == OP_PHI, "the materialised Pi serves Phi only");
     constexpr int NG = THREADS / G;
     constexpr int NWARPS = THREADS / 32;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
     if (a.inner && a.inner->done) return true;
-    const int nm1 = NM1 > 0 ? NM1 : a.nm1;
+    const int nm1 = PI ? 0 : (NM1 > 0 ? NM1 : a.nm1);  // staged coordinate streams
     const int tid = threadIdx.x;
     const int g = tid / G, lane = tid % G;
     const int warp = tid >> 5, wlane = tid & 31;
@@ -601,12 +628,20 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             const bool fast = q + U <= lb && rr[U - 1] == cur;
 
             T pi[U][RPL];
+            if constexpr (PI) {
+                // consecutive rows of the materialised Pi, streamed (read once per Phi)
+                const T *P = reinterpret_cast<const T *>(a.pi) + (p0 + q) * Rp + col0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                load_row<T, RPL>(reinterpret_cast<const T *>(a.A[0]) + (int64_t)ii[u][0] * Rp + col0, pi[u]);
+                for (int u = 0; u < U; ++u) load_row_stream<T, RPL>(P + (int64_t)min(u, lb - 1 - q) * Rp, pi[u]);
+            } else {
 #pragma unroll
-                for (int k = 1; k < MAXK; ++k)
-                    if (k < nm1) mul_row<T, RPL>(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[u][k] * Rp + col0, pi[u]);
+                for (int u = 0; u < U; ++u) {
+                    load_row<T, RPL>(reinterpret_cast<const T *>(a.A[0]) + (int64_t)ii[u][0] * Rp + col0, pi[u]);
+#pragma unroll
+                    for (int k = 1; k < MAXK; ++k)
+                        if (k < nm1)
+                            mul_row<T, RPL>(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[u][k] * Rp + col0, pi[u]);
+                }
             }
             T v[U];
             if (OP == OP_MTTKRP) {
@@ -833,7 +868,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 }
 
 // One block per tile of one tensor.
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI>
 __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[THREADS / 32];
@@ -841,13 +876,13 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     if (threadIdx.x == 0) stage_barrier_init(&bar);
     __syncthreads();
     uint32_t phase = 0;
-    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI>(a, blockIdx.x, smem_raw, red, &bar, phase);
 }
 
 // The same with registers held to four resident blocks per SM (64 per
 // thread at 256 threads): measured on GB300 the better trade for FP32 with
 // one float4 per lane, where more warps hide more gather latency.
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U>
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI>
 __global__ void __launch_bounds__(THREADS, 4) phi_tile_kernel_occ4(const PhiArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[THREADS / 32];
@@ -855,7 +890,47 @@ __global__ void __launch_bounds__(THREADS, 4) phi_tile_kernel_occ4(const PhiArgs
     if (threadIdx.x == 0) stage_barrier_init(&bar);
     __syncthreads();
     uint32_t phase = 0;
-    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U>(a, blockIdx.x, smem_raw, red, &bar, phase);
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI>(a, blockIdx.x, smem_raw, red, &bar, phase);
+}
+
+// Materialised Khatri-Rao rows, the paper's Pi (Algorithm 3 reads Pi[j][r]):
+// Pi[p][:] = A^(m_0)[i_m0(p), :] * A^(m_1)[i_m1(p), :] * ... over the modes
+// m != n, for every nonzero p in mode-n order.  The products are taken in the
+// same order as the fused tile kernel forms them, so a Phi from the
+// materialised Pi equals the fused one bit for bit.  One thread per 16-byte
+// vector of a row; rows are written with evict-first stores (read once per
+// inner iteration, they are not worth keeping in L2).
+template <typename T, int NM1>
+__global__ void __launch_bounds__(256) pi_build_kernel(const PhiArgs a, T *__restrict__ pi) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
+    const int nm1 = NM1 > 0 ? NM1 : a.nm1;
+    const int vpr = a.Rp / VN;  // vectors per row
+    const int64_t total = a.nnz * vpr;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / vpr;
+        const int c = (int)(e - p * vpr) * VN;
+        V x = __ldg(reinterpret_cast<const V *>(reinterpret_cast<const T *>(a.A[0]) +
+                                                (int64_t)__ldg(a.idx[0] + p) * a.Rp + c));
+#pragma unroll
+        for (int k = 1; k < MAXK; ++k) {
+            if (k < nm1) {
+                const V y = __ldg(reinterpret_cast<const V *>(reinterpret_cast<const T *>(a.A[k]) +
+                                                              (int64_t)__ldg(a.idx[k] + p) * a.Rp + c));
+                if constexpr (VN == 4) {
+                    x.x *= y.x;
+                    x.y *= y.y;
+                    x.z *= y.z;
+                    x.w *= y.w;
+                } else {
+                    x.x *= y.x;
+                    x.y *= y.y;
+                }
+            }
+        }
+        __stcs(reinterpret_cast<V *>(pi + p * a.Rp + c), x);
+    }
 }
 
 // FP32 with one float4 per lane runs at four blocks per SM

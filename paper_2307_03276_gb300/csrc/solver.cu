@@ -86,6 +86,9 @@ static cpapr_status enqueue_mode(cpapr_ctx *ctx, int n, double tol, int max_inne
     InnerState *inner = ctx->inner + n;
     CPAPR_TRY(launch_sb(ctx, n, shift, inner));
     CPAPR_TRY(launch_empty_kkt(ctx, n, ctx->B, inner));
+    // the other modes' factors are fixed for this inner loop: their
+    // Khatri-Rao rows are built once here if the mode streams them
+    CPAPR_TRY(launch_pi_build(ctx, n));
     if (ctx->opt.use_graph) {
         CPAPR_TRY(build_inner_graph(ctx, n, tol, max_inner));
         CPAPR_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec[n], ctx->stream));
@@ -249,13 +252,22 @@ cpapr_status autotune(cpapr_ctx *ctx) {
         CPAPR_TRY(launch_scale_b(ctx, n, ctx->B));
         float best = 1e30f;
         int bl = ctx->mode[n].lanes, bt = ctx->mode[n].tile_nnz, br = ctx->mode[n].reduction;
+        int bp = ctx->mode[n].pi;
         const int tiles[] = {1024, 2048, 4096, 8192};
+        // the materialised Khatri-Rao rows are a candidate where their buffer
+        // fits (the fixed cost of building them once per inner loop is not
+        // timed: it is spread over the inner iterations)
+        const int npi = pi_fits(ctx) ? 2 : 1;
         for (int lanes = 1; lanes <= 32; lanes <<= 1) {
             if (!phi_config_supported((int)ctx->esize, ctx->N - 1, Rp, lanes)) continue;
             for (int tile : tiles) {
                 if (phi_smem_for((int)ctx->esize, ctx->N - 1, tile, Rp, lanes) > kMaxPhiSmem) continue;
-                for (int red = CPAPR_REDUCE_ATOMIC; red <= CPAPR_REDUCE_SEGMENTED; ++red) {
+                for (int cand = 0; cand < 2 * npi; ++cand) {
+                    const int red = cand % 2 ? CPAPR_REDUCE_SEGMENTED : CPAPR_REDUCE_ATOMIC;
+                    const int pi = cand / 2;
                     CPAPR_TRY(configure_mode(ctx, n, lanes, tile, red));
+                    CPAPR_TRY(configure_pi(ctx, n, pi));
+                    if (pi) CPAPR_TRY(launch_pi_build(ctx, n));
                     CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, nullptr));
                     CPAPR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
                     for (int rep = 0; rep < 3; ++rep) CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, nullptr));
@@ -268,11 +280,13 @@ cpapr_status autotune(cpapr_ctx *ctx) {
                         bl = lanes;
                         bt = tile;
                         br = red;
+                        bp = pi;
                     }
                 }
             }
         }
         CPAPR_TRY(configure_mode(ctx, n, bl, bt, br));
+        CPAPR_TRY(configure_pi(ctx, n, bp));
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

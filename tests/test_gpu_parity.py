@@ -71,12 +71,16 @@ def model_for(T, seed=5):
 CASES = ["c1", "c2s", "c3s", "c5s", "c5s64", "n2", "n6"]
 
 
+PI_MODES = [cpapr.CPAPR_PI_FUSED, cpapr.CPAPR_PI_MATERIALISED]
+
+
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("reduction", [cpapr.CPAPR_REDUCE_SEGMENTED, cpapr.CPAPR_REDUCE_ATOMIC])
-def test_phi_fp64_matches_oracle(name, reduction):
+@pytest.mark.parametrize("pi_mode", PI_MODES)
+def test_phi_fp64_matches_oracle(name, reduction, pi_mode):
     T = case(name)
     lam, fs = model_for(T)
-    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, reduction=reduction) as t:
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, reduction=reduction, pi_mode=pi_mode) as t:
         t.set_model(lam, fs)
         for n in range(T.nmodes):
             want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
@@ -382,6 +386,50 @@ def test_ranks_not_power_of_two(rank):
             for n in range(3):
                 want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
                 assert max_rel(t.phi(n), want) <= tol, (rank, prec, n)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s64", "n6"])
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_materialised_pi_equals_fused(name, precision):
+    """Phi from the materialised Khatri-Rao rows (Algorithm 3's Pi, built
+    once per mode) is bit-identical to Phi with the rows formed per nonzero:
+    the products are taken in the same order and the Phi arithmetic is the
+    same.  The info block reports the choice."""
+    T = case(name)
+    lam, fs = model_for(T, 12)
+    got = {}
+    for pm in PI_MODES:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, pi_mode=pm) as t:
+            t.set_model(lam, fs)
+            info = t.info()
+            assert list(info.pi_mode)[:T.nmodes] == [pm] * T.nmodes
+            got[pm] = [t.phi(n) for n in range(T.nmodes)]
+    for n in range(T.nmodes):
+        assert np.array_equal(got[PI_MODES[0]][n], got[PI_MODES[1]][n]), (name, n)
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_mu_solve_materialised_pi_equals_fused(use_graph):
+    """A whole MU solve (S, B, inner loops with the KKT check, normalisation)
+    ends in the same model whether Pi is materialised or fused, and matches
+    the oracle."""
+    T = case("c3s")
+    lam, fs = model_for(T, 13)
+    res = {}
+    for pm in PI_MODES:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pm, use_graph=use_graph) as t:
+            t.set_model(lam, fs)
+            r = t.mu_solve(tol=1e-4, max_outer=2, max_inner=5)
+            res[pm] = (r, t.get_model())
+    (r0, (l0, f0)), (r1, (l1, f1)) = res[PI_MODES[0]], res[PI_MODES[1]]
+    assert r0["total_inner"] == r1["total_inner"]
+    assert np.array_equal(l0, l1)
+    for a, b in zip(f0, f1):
+        assert np.array_equal(a, b)
+    want = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=2, max_inner=5)
+    assert max_rel(l1, want["lambda"]) <= 1e-10
+    for A, Ar in zip(f1, want["factors"]):
+        np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
 
 
 def test_tile_size_limits():
