@@ -67,22 +67,30 @@ def load_peaks() -> dict:
 # byte and FLOP models (per Phi^(n) launch over the whole tensor)
 # ---------------------------------------------------------------------------
 
-def phi_bytes(dims, nnz, R, n, value_bytes, factor_bytes) -> float:
-    """Compulsory HBM bytes of one Phi^(n): the mode-n index and value streams,
-    the row offsets, one read of every other factor and of B, one write of Phi."""
+def phi_bytes(dims, nnz, R, n, value_bytes, factor_bytes, materialised=False) -> float:
+    """Compulsory HBM bytes of one Phi^(n).  Fused Khatri-Rao rows: the mode-n
+    index and value streams, the row offsets, one read of every other factor
+    and of B, one write of Phi.  Materialised rows (the paper's Pi): the row
+    ids and values, the Pi stream (R values per nonzero), one read of B and
+    one write of Phi."""
     N = len(dims)
+    if materialised:
+        return nnz * (4 + value_bytes + R * factor_bytes) + factor_bytes * R * 2 * dims[n]
     other = sum(dims) - dims[n]
     return nnz * (4 * (N - 1) + value_bytes) + 4 * (dims[n] + 1) + factor_bytes * R * (other + 2 * dims[n])
 
 
-def phi_flops(N, nnz, R) -> float:
-    """(N-2)R Khatri-Rao products, 2R dot, max + divide, 2R scale-add per nonzero."""
-    return nnz * ((N + 2) * R + 2)
+def phi_flops(N, nnz, R, materialised=False) -> float:
+    """Fused: (N-2)R Khatri-Rao products, 2R dot, max + divide, 2R scale-add
+    per nonzero.  Materialised: the products are done once per inner loop by
+    the Pi build, so a Phi costs 4R + 2 (the paper's own count)."""
+    return nnz * (4 * R + 2) if materialised else nnz * ((N + 2) * R + 2)
 
 
-def phi_l2_bytes(N, nnz, R, factor_bytes) -> float:
-    """Factor-row bytes gathered per Phi^(n): N-1 other rows and the B row per nonzero."""
-    return nnz * N * R * factor_bytes
+def phi_l2_bytes(N, nnz, R, factor_bytes, materialised=False) -> float:
+    """Factor-row bytes gathered per Phi^(n): N-1 other rows and the B row per
+    nonzero (fused); the B row alone with materialised rows."""
+    return nnz * (1 if materialised else N) * R * factor_bytes
 
 
 # ---------------------------------------------------------------------------
@@ -230,10 +238,10 @@ def cpu_baseline(T, lam, fs, seconds: float = 10.0, sample: int = 1_000_000) -> 
 # our arm
 # ---------------------------------------------------------------------------
 
-def timed_solve(cp, torch, T, lam, fs, precision, steps, warmup, dist, use_cuda, clocks=None):
+def timed_solve(cp, torch, T, lam, fs, precision, steps, warmup, dist, use_cuda, clocks=None, pi_mode=0):
     stream = torch.cuda.current_stream()
     t = cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, profile=1, use_graph=0,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, pi_mode=pi_mode)
     t.set_model(lam, fs)
     for _ in range(warmup):
         t.mu_solve(TOL, 1, MAX_INNER, trace=True, ll_trace=False)
@@ -323,27 +331,32 @@ def kernel_breakdown(stats, steps):
     return {KERNEL_NAMES[k]: stats[k][1] / steps for k in range(7) if stats[k][0]}
 
 
-def roofline_for(T, inner_per_mode, stats, precision, peaks, cp):
-    """Roofline of the Phi tile kernel from its measured average duration."""
+def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None):
+    """Roofline of the Phi tile kernel from its measured average duration.
+    pi_modes: per mode, whether Phi streamed materialised Khatri-Rao rows."""
     N, nnz, R = T.nmodes, T.nnz, T.rank
     fb = 8 if precision == cp.CPAPR_FP64 else 4
+    mat = [bool(pi_modes and pi_modes[n] == cp.CPAPR_PI_MATERIALISED) for n in range(N)]
     launches, total_ms = stats[cp.K_PHI]
-    byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb) for n in range(N))
-    fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R) for n in range(N))
-    l2 = sum(inner_per_mode[n] * phi_l2_bytes(N, nnz, R, fb) for n in range(N))
+    byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb, mat[n]) for n in range(N))
+    fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R, mat[n]) for n in range(N))
+    l2 = sum(inner_per_mode[n] * phi_l2_bytes(N, nnz, R, fb, mat[n]) for n in range(N))
     sec = total_ms / 1e3
     hbm = {"achieved": byts / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
     l2g = {"achieved": l2 / sec / 1e9, "peak": L2_GATHER_GBS, "unit": "GB/s"}
     l2g["frac"] = l2g["achieved"] / l2g["peak"]
+    form = "materialised Pi" if all(mat) else ("fused Pi" if not any(mat) else "mixed")
     if precision == cp.CPAPR_FP64:
         ach = fl / sec / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "phi_tile_kernel<double>", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+                "kernel": f"phi_tile_kernel<double> ({form})",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                "flop_model": "4R+2 per nonzero" if all(mat) else "(N+2)R+2 per nonzero"}
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
-                "frac": hbm["frac"], "traffic": None, "kernel": "phi_tile_kernel<float>",
+                "frac": hbm["frac"], "traffic": None, "kernel": f"phi_tile_kernel<float> ({form})",
                 "peak_source": f"{peaks['source']} hbm_gbs"}
     roof["avg_launch_ms"] = total_ms / max(launches, 1)
     roof["launches"] = launches
@@ -420,7 +433,7 @@ def run_ours(args):
     res = timed_solve(cp, torch, T, lam, fs, prim, args.steps, args.warmup, dist, use_cuda, clocks)
     units = float(res["inner"].sum()) * T.nnz
     units_all, sec = aggregate(dist, units, res["ms"] / 1e3, use_cuda)
-    roof = roofline_for(T, res["inner"], res["stats"], prim, peaks, cp)
+    roof = roofline_for(T, res["inner"], res["stats"], prim, peaks, cp, list(res["info"].pi_mode)[:T.nmodes])
     out = {"metric": METRIC, "value": units_all / sec, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prim == cp.CPAPR_FP64 else "f32",
@@ -443,12 +456,25 @@ def run_ours(args):
         name = "fp32" if other == cp.CPAPR_FP32 else "fp64"
         out["variants"] = {name: {"value": u2 / s2, "unit": UNIT, "ms_per_step": s2 * 1e3 / args.steps,
                                   "dtype": "f32" if other == cp.CPAPR_FP32 else "f64",
-                                  "roofline": roofline_for(T, r2["inner"], r2["stats"], other, peaks, cp),
+                                  "roofline": roofline_for(T, r2["inner"], r2["stats"], other, peaks, cp,
+                                                           list(r2["info"].pi_mode)[:T.nmodes]),
                                   "inner_iterations_per_mode": r2["inner"].tolist(),
                                   "kernel_ms_per_step": kernel_breakdown(r2["stats"], args.steps),
                                   "loglik_last": r2["last"]["loglik"]}}
         mt_l, mt_ms = r2["mttkrp"]
         kern["mttkrp_" + name] = {"nnz_per_s": T.nnz * mt_l / (mt_ms / 1e3), "avg_launch_ms": mt_ms / max(mt_l, 1)}
+        if prim == cp.CPAPR_FP64 and T.nmodes >= 3:
+            # the same FP64 step with the Khatri-Rao rows formed inside every Phi
+            r3 = timed_solve(cp, torch, T, lam, fs, prim, args.steps, args.warmup, dist, use_cuda,
+                             pi_mode=cp.CPAPR_PI_FUSED)
+            u3, s3 = aggregate(dist, float(r3["inner"].sum()) * T.nnz, r3["ms"] / 1e3, use_cuda)
+            out["variants"]["fp64_fused_pi"] = {
+                "value": u3 / s3, "unit": UNIT, "ms_per_step": s3 * 1e3 / args.steps, "dtype": "f64",
+                "roofline": roofline_for(T, r3["inner"], r3["stats"], prim, peaks, cp,
+                                         list(r3["info"].pi_mode)[:T.nmodes]),
+                "inner_iterations_per_mode": r3["inner"].tolist(),
+                "kernel_ms_per_step": kernel_breakdown(r3["stats"], args.steps),
+                "loglik_last": r3["last"]["loglik"]}
         for pname, prec in (("fp64", cp.CPAPR_FP64), ("fp32", cp.CPAPR_FP32)):
             b = batched_run(cp, torch, prec, args.steps, args.warmup)
             ub, sb = aggregate(dist, b["batched"]["value"] * b["batched"]["ms_per_step"] * args.steps / 1e3,

@@ -89,8 +89,9 @@ enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
  *             inner loop) into a buffer of nnz x R values of the working
  *             precision, which every Phi of the inner loop streams; results
  *             are identical to the fused form.  CPAPR_PI_AUTO (default):
- *             materialised in FP64 with three or more modes when the buffer
- *             takes at most half of the free device memory, else fused.
+ *             materialised in FP64 with three or more modes and in FP32 with
+ *             four or more, when the buffer takes at most half of the free
+ *             device memory; else fused.
  *             MTTKRP, the log-likelihood and the batched solver always form
  *             the rows in place.
  */

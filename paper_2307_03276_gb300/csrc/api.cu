@@ -145,28 +145,28 @@ static int next_pow2(int v) {
 
 // Built-in choice of lanes per nonzero and nonzeros per tile (from sweeps on
 // GB300 over the 1e7-nonzero 3-way and 5e7-nonzero 4-way workloads).  FP64:
-// one lane per nonzero up to 16 ranks (no shuffle adds on the scarce FP64
-// pipe), 8 ranks per lane above with batches of four nonzeros; FP32: 16-byte
-// vectors of 4 ranks per lane up to 32 ranks, 8 ranks per lane above, and the
-// largest tile whose shared-memory stage leaves room for the blocks per SM
-// the tile kernel is built for (four with one float4 per lane, else three).
-static void heuristic_config(const cpapr_ctx *ctx, int n, int *lanes, int *tile, int *reduction) {
+// 8 ranks per lane (one lane up to 8 ranks) with batches of up to four
+// nonzeros; FP32: 16-byte vectors of 4 ranks per lane up to 32 ranks, 8 ranks
+// per lane above, and the largest tile whose shared-memory stage leaves room
+// for the blocks per SM the tile kernel is built for (four with one float4 per
+// lane, else three).  With materialised Khatri-Rao rows the stage holds only
+// row ids and values, so the same room takes larger tiles.
+static void heuristic_config(const cpapr_ctx *ctx, int n, int pi, int *lanes, int *tile, int *reduction) {
     const int Rp = ctx->Rp;
     int g;
     if (ctx->esize == 8)
-        g = Rp <= 16 ? 1 : Rp / 8;
+        g = std::max(1, Rp / 8);
     else
         g = Rp <= 32 ? std::max(1, Rp / 4) : Rp / 8;
     *lanes = g;
     if (ctx->esize == 8) {
         *tile = Rp <= 16 ? 2048 : 1024;
     } else {
-        // the largest tile whose shared-memory stage still lets the kernel's
-        // resident blocks (4 with one float4 per lane, else 3) share an SM
+        const int nm1 = pi ? 0 : ctx->N - 1;
         const size_t per_block = (Rp / g <= 4 ? 227 / 4 : 227 / 3) * 1024 - 1024;
         *tile = 1024;
         for (int t : {4096, 2048})
-            if (phi_smem_for(4, ctx->N - 1, t, Rp, g) <= per_block) {
+            if (phi_smem_for(4, nm1, t, Rp, g) <= per_block) {
                 *tile = t;
                 break;
             }
@@ -233,9 +233,11 @@ int pi_fits(const cpapr_ctx *ctx) {
     return (double)ctx->nnz_pad * ctx->Rp * ctx->esize <= 0.5 * (double)freeb ? 1 : 0;
 }
 
-// Automatic choice: materialise in FP64, where the products cost time on the
-// narrow FP64 pipe; the FP32 form gathers and multiplies in place.
-int pi_auto(const cpapr_ctx *ctx) { return ctx->esize == 8 ? pi_fits(ctx) : 0; }
+// Automatic choice (from GB300 sweeps): materialise in FP64, where the
+// products cost time on the narrow FP64 pipe, and in FP32 from four modes on,
+// where streaming one row beats gathering three or more; a 3-way FP32 Phi
+// gathers and multiplies in place.
+int pi_auto(const cpapr_ctx *ctx) { return (ctx->esize == 8 || ctx->N >= 4) ? pi_fits(ctx) : 0; }
 
 cpapr_status autotune(cpapr_ctx *ctx);
 
@@ -387,12 +389,13 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
 
     for (int n = 0; n < nmodes; ++n) {
         int lanes, tile, red;
-        heuristic_config(ctx, n, &lanes, &tile, &red);
+        const int pi = o.pi_mode == CPAPR_PI_MATERIALISED ? 1 : o.pi_mode == CPAPR_PI_FUSED ? 0 : pi_auto(ctx);
+        heuristic_config(ctx, n, pi, &lanes, &tile, &red);
         if (o.rank_lanes) lanes = o.rank_lanes;
         if (o.tile_nnz) tile = o.tile_nnz;
         if (o.reduction) red = o.reduction;
         CR_TRY(configure_mode(ctx, n, lanes, tile, red));
-        CR_TRY(configure_pi(ctx, n, o.pi_mode == CPAPR_PI_MATERIALISED ? 1 : o.pi_mode == CPAPR_PI_FUSED ? 0 : pi_auto(ctx)));
+        CR_TRY(configure_pi(ctx, n, pi));
     }
     if (o.autotune) CR_TRY(autotune(ctx));
     e = cudaStreamSynchronize(ctx->stream);

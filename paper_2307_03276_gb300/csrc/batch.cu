@@ -56,8 +56,8 @@ struct BatchCtl {
 
 // rank classes of the batched Phi kernel: (ranks per lane, lanes), ranks up
 // to 32.  All classes are inlined into one kernel, so its registers are the
-// largest class's: FP32 keeps one float4 per lane; FP64 one lane up to 16
-// ranks and four lanes of 8 ranks for 32 (the single-tensor heuristic's choices).
+// largest class's: FP32 keeps one float4 per lane; FP64 one lane up to 8
+// ranks and lanes of 8 ranks above (the single-tensor heuristic's choices).
 template <typename T> struct Classes;
 template <> struct Classes<float> {
     static constexpr int n = 4;
@@ -66,8 +66,8 @@ template <> struct Classes<float> {
 };
 template <> struct Classes<double> {
     static constexpr int n = 5;
-    static constexpr int rpl[n] = {2, 4, 8, 16, 8};
-    static constexpr int g[n] = {1, 1, 1, 1, 4};
+    static constexpr int rpl[n] = {2, 4, 8, 8, 8};
+    static constexpr int g[n] = {1, 1, 1, 2, 4};
 };
 
 template <typename T>
