@@ -546,6 +546,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.inner = c->inner + n;
             a.llpart = c->llpart;
             a.err = c->errflag + 3;
+            a.stage_extra = injected_stage_shortfall();
             d.cfg = class_for<T>(c->Rp);
             d.rp = c->Rp;
             d.rows = c->dims[n];

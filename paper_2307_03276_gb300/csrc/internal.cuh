@@ -165,6 +165,8 @@ cpapr_status launch_pi_build(cpapr_ctx *ctx, int n);
 cpapr_status configure_pi(cpapr_ctx *ctx, int n, int on);
 int pi_auto(const cpapr_ctx *ctx);
 int pi_fits(const cpapr_ctx *ctx);
+// bytes the staging barrier of the tile kernels expects beyond its copies (failure injection; 0 normally)
+uint32_t injected_stage_shortfall();
 // Sum of x log(m) over nonzeros, into llpart then *dst (device double).
 cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
 // Rows of mode n without nonzeros: zero them in `out`; add their KKT term

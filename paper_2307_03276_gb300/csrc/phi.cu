@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "phi_kernels.cuh"
 
@@ -58,6 +59,16 @@ static cudaError_t dispatch(const cpapr_ctx *ctx, const PhiArgs &a, int rpl, int
     }
 }
 
+// Host-side failure injection for the bounded staging wait: while the
+// environment variable CPAPR_FAULT_STAGE_WAIT is "1", every tile's barrier
+// expects 16 bytes more than its copies bring, so the wait runs out after
+// its time limit, the tile is skipped and the call reports CPAPR_E_TIMEOUT.
+// Nothing faults: the copies themselves are the normal ones.
+uint32_t injected_stage_shortfall() {
+    const char *s = std::getenv("CPAPR_FAULT_STAGE_WAIT");
+    return (s && s[0] == '1' && s[1] == 0) ? 16u : 0u;
+}
+
 static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerState *inner) {
     const ModeLayout &L = ctx->mode[n];
     PhiArgs a{};
@@ -88,6 +99,7 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.inner = inner;
     a.llpart = ctx->llpart;
     a.err = ctx->errflag + 3;
+    a.stage_extra = injected_stage_shortfall();
     return a;
 }
 

@@ -74,6 +74,8 @@ struct PhiArgs {
     double *llpart;     // OP_LL: one partial per tile
     int32_t *err;       // set to 1 when a bounded wait gives up
     const void *pi;     // materialised Khatri-Rao rows [nnz][Rp] in mode-n order, or null
+    uint32_t stage_extra;  // bytes the staging barrier expects beyond the copies: 0, or 16
+                           // when the host injects a staging-wait failure (tests)
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -490,7 +492,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const uint32_t b4 = (uint32_t)(((int64_t)n * 4 + 15) & ~(int64_t)15);
         const uint32_t bv = (uint32_t)(((int64_t)n * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
-        stage_expect(bar, b4 * (uint32_t)(nm1 + 1) + bv);
+        stage_expect(bar, b4 * (uint32_t)(nm1 + 1) + bv + a.stage_extra);
         stage_copy(s_rid, a.rid + p0, b4, bar);
         for (int k = 0; k < nm1; ++k) stage_copy(s_idx + (int64_t)k * cap, a.idx[k] + p0, b4, bar);
         stage_copy(s_val, reinterpret_cast<const T *>(a.val) + p0, bv, bar);

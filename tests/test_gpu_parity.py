@@ -433,6 +433,26 @@ def test_mu_solve_materialised_pi_equals_fused(use_graph):
         np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
 
 
+def test_staging_wait_timeout_is_reported(monkeypatch):
+    """The tile kernels' one wait (for a tile's bulk copies into shared
+    memory) is bounded in time.  With the host-side injection every tile's
+    barrier expects 16 bytes more than its copies bring: the wait runs out
+    after its limit (about a second), the tile is skipped, the call reports
+    CPAPR_E_TIMEOUT (6), and the context stays usable.  Nothing faults."""
+    T = synth.random_tensor((60, 50, 40), 3_000, 8, 91)
+    lam, fs = model_for(T, 14)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=4096, pi_mode=cpapr.CPAPR_PI_FUSED) as t:
+        t.set_model(lam, fs)
+        assert t.info().ntiles[0] == 1
+        monkeypatch.setenv("CPAPR_FAULT_STAGE_WAIT", "1")
+        with pytest.raises(cpapr.CpaprError) as e:
+            t.phi(0)
+        assert e.value.status == 6
+        monkeypatch.delenv("CPAPR_FAULT_STAGE_WAIT")
+        want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[0] * lam[None, :], 0)
+        assert max_rel(t.phi(0), want) <= 1e-12
+
+
 def test_tile_size_limits():
     """A tile's staged streams must fit in shared memory and start on 16-byte
     boundaries: the largest 3-way FP64 tile works, larger or odd sizes are
