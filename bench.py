@@ -52,6 +52,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_GATHER_GBS = 7450.0
 
 
+# DRAM bytes per Phi launch by mode (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# (--set full, the second pass of bench.py --kernel-only) of the kernel configuration named in the key
+# (workload, dtype, Pi form, lanes per mode, tile per mode); a run in any other configuration reports
+# traffic null, and an entry is dropped when its kernel changes.
+NCU_TRAFFIC = {
+    ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
+        ([2.8326e9, 2.8259e9, 2.7646e9], "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"),
+    ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
+        ([202.1e6, 201.0e6, 197.4e6], "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"),
+}
+
+
 def load_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -331,12 +343,27 @@ def kernel_breakdown(stats, steps):
     return {KERNEL_NAMES[k]: stats[k][1] / steps for k in range(7) if stats[k][0]}
 
 
-def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None):
+def ncu_traffic(T, dtype, mat, info, inner_per_mode):
+    """Measured DRAM bytes per Phi launch for this configuration, weighted by
+    the launches of each mode, with its source; (None, None) if not captured."""
+    N = T.nmodes
+    form = "materialised" if all(mat) else ("fused" if not any(mat) else "mixed")
+    key = (T.name, dtype, form, tuple(info.rank_lanes)[:N], tuple(info.tile_nnz)[:N])
+    if key not in NCU_TRAFFIC:
+        return None, None
+    per_mode, src = NCU_TRAFFIC[key]
+    w = [float(inner_per_mode[n]) for n in range(N)]
+    return sum(w[n] * per_mode[n] for n in range(N)) / max(sum(w), 1.0), src
+
+
+def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, info=None):
     """Roofline of the Phi tile kernel from its measured average duration.
     pi_modes: per mode, whether Phi streamed materialised Khatri-Rao rows."""
     N, nnz, R = T.nmodes, T.nnz, T.rank
     fb = 8 if precision == cp.CPAPR_FP64 else 4
     mat = [bool(pi_modes and pi_modes[n] == cp.CPAPR_PI_MATERIALISED) for n in range(N)]
+    traffic, traffic_src = (ncu_traffic(T, "f64" if fb == 8 else "f32", mat, info, inner_per_mode)
+                            if info is not None else (None, None))
     launches, total_ms = stats[cp.K_PHI]
     byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb, mat[n]) for n in range(N))
     fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R, mat[n]) for n in range(N))
@@ -350,14 +377,17 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None):
     if precision == cp.CPAPR_FP64:
         ach = fl / sec / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": f"phi_tile_kernel<double> ({form})",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
                 "flop_model": "4R+2 per nonzero" if all(mat) else "(N+2)R+2 per nonzero"}
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
-                "frac": hbm["frac"], "traffic": None, "kernel": f"phi_tile_kernel<float> ({form})",
+                "frac": hbm["frac"], "traffic": traffic, "kernel": f"phi_tile_kernel<float> ({form})",
                 "peak_source": f"{peaks['source']} hbm_gbs"}
+    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    roof["traffic_source"] = traffic_src
+    roof["algorithmic_bytes_per_launch"] = byts / max(sum(inner_per_mode[n] for n in range(N)), 1)
     roof["avg_launch_ms"] = total_ms / max(launches, 1)
     roof["launches"] = launches
     roof["hbm"] = hbm
@@ -433,7 +463,8 @@ def run_ours(args):
     res = timed_solve(cp, torch, T, lam, fs, prim, args.steps, args.warmup, dist, use_cuda, clocks)
     units = float(res["inner"].sum()) * T.nnz
     units_all, sec = aggregate(dist, units, res["ms"] / 1e3, use_cuda)
-    roof = roofline_for(T, res["inner"], res["stats"], prim, peaks, cp, list(res["info"].pi_mode)[:T.nmodes])
+    roof = roofline_for(T, res["inner"], res["stats"], prim, peaks, cp, list(res["info"].pi_mode)[:T.nmodes],
+                        res["info"])
     out = {"metric": METRIC, "value": units_all / sec, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prim == cp.CPAPR_FP64 else "f32",
@@ -457,7 +488,7 @@ def run_ours(args):
         out["variants"] = {name: {"value": u2 / s2, "unit": UNIT, "ms_per_step": s2 * 1e3 / args.steps,
                                   "dtype": "f32" if other == cp.CPAPR_FP32 else "f64",
                                   "roofline": roofline_for(T, r2["inner"], r2["stats"], other, peaks, cp,
-                                                           list(r2["info"].pi_mode)[:T.nmodes]),
+                                                           list(r2["info"].pi_mode)[:T.nmodes], r2["info"]),
                                   "inner_iterations_per_mode": r2["inner"].tolist(),
                                   "kernel_ms_per_step": kernel_breakdown(r2["stats"], args.steps),
                                   "loglik_last": r2["last"]["loglik"]}}
@@ -471,7 +502,7 @@ def run_ours(args):
             out["variants"]["fp64_fused_pi"] = {
                 "value": u3 / s3, "unit": UNIT, "ms_per_step": s3 * 1e3 / args.steps, "dtype": "f64",
                 "roofline": roofline_for(T, r3["inner"], r3["stats"], prim, peaks, cp,
-                                         list(r3["info"].pi_mode)[:T.nmodes]),
+                                         list(r3["info"].pi_mode)[:T.nmodes], r3["info"]),
                 "inner_iterations_per_mode": r3["inner"].tolist(),
                 "kernel_ms_per_step": kernel_breakdown(r3["stats"], args.steps),
                 "loglik_last": r3["last"]["loglik"]}
@@ -516,6 +547,69 @@ def run_kernel_only(args):
                       "tile_nnz": list(info.tile_nnz)[:T.nmodes], "rank_lanes": list(info.rank_lanes)[:T.nmodes]}))
 
 
+def run_r_sweep(args):
+    """Phi^(n) and MTTKRP over R in {8, 16, 32, 64} on one tensor (default: the
+    5-way 5e4 x 5e4 x 5e3 x 1e3 x 24 workload, 1e8 nonzeros), each rank with the
+    autotuner choosing lanes, tile, reduction and Pi form per mode; one JSON
+    line with nonzeros/s and the roofline fractions per rank and precision."""
+    import torch
+    from paper_2307_03276_gb300 import build, cpapr as cp, synth
+    torch.cuda.set_device(0)
+    build.build()
+    peaks = load_peaks()
+    spec = synth.SPECS[args.workload]
+    T = synth.generate(spec)
+    N = T.nmodes
+    ranks = [int(r) for r in args.ranks.split(",")]
+    precs = [cp.CPAPR_FP64, cp.CPAPR_FP32] if args.precision == "both" else (
+        [cp.CPAPR_FP64] if args.precision == "fp64" else [cp.CPAPR_FP32])
+    out = {"sweep": "rank", "workload": T.name, "dims": list(T.dims), "nnz": T.nnz, "results": []}
+    for R in ranks:
+        fs = synth.random_factors(T.dims, R, spec.seed + 17)
+        lam = np.ones(R)
+        for prec in precs:
+            fb = 8 if prec == cp.CPAPR_FP64 else 4
+            with cp.Tensor(T.dims, T.idx, T.vals, R, precision=prec, profile=1, use_graph=0, autotune=1) as t:
+                info = t.info()
+                t.set_model(lam, fs)
+                for n in range(N):
+                    t.phi(n)
+                for k in range(7):
+                    t.kernel_stats(k, reset=True)
+                reps = max(1, args.steps)
+                for _ in range(reps):
+                    for n in range(N):
+                        t.phi(n)
+                for n in range(N):
+                    t.mttkrp(n)
+                for _ in range(reps):
+                    for n in range(N):
+                        t.mttkrp(n)
+                pl, pms = t.kernel_stats(cp.K_PHI)
+                bl, bms = t.kernel_stats(cp.K_PI)
+                ml, mms = t.kernel_stats(cp.K_MTTKRP)
+                pim = list(info.pi_mode)[:N]
+            mat = [m == cp.CPAPR_PI_MATERIALISED for m in pim]
+            per = pms / max(pl, 1)
+            byts = sum(phi_bytes(T.dims, T.nnz, R, n, fb, fb, mat[n]) for n in range(N)) / N
+            fl = sum(phi_flops(N, T.nnz, R, mat[n]) for n in range(N)) / N
+            mb = sum(phi_bytes(T.dims, T.nnz, R, n, fb, fb, False) for n in range(N)) / N
+            mper = mms / max(ml, 1)
+            row = {"rank": R, "dtype": "f64" if prec == cp.CPAPR_FP64 else "f32",
+                   "rank_lanes": list(info.rank_lanes)[:N], "tile_nnz": list(info.tile_nnz)[:N],
+                   "reduction": list(info.reduction)[:N], "pi_mode": pim,
+                   "phi_ms_per_launch": per, "phi_nnz_per_s": T.nnz / (per / 1e3),
+                   "phi_hbm_frac": byts / (per / 1e3) / 1e9 / peaks["hbm_gbs"],
+                   "phi_fp64_frac": (fl / (per / 1e3) / 1e12 / FP64_PEAK_TFLOPS) if fb == 8 else None,
+                   "pi_build_ms_per_launch": (bms / bl) if bl else None,
+                   "mttkrp_ms_per_launch": mper, "mttkrp_nnz_per_s": T.nnz / (mper / 1e3),
+                   "mttkrp_hbm_frac": mb / (mper / 1e3) / 1e9 / peaks["hbm_gbs"]}
+            out["results"].append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    out["peaks"] = {"hbm_gbs": peaks["hbm_gbs"], "source": peaks["source"], "fp64_tflops": FP64_PEAK_TFLOPS}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores, on bounded samples of the same workload."""
     world, rank, _ = dist_env()
@@ -556,15 +650,27 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "both"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--r-sweep", action="store_true",
+                    help="Phi and MTTKRP over --ranks on --workload (default c5) with autotuned choices")
+    ap.add_argument("--ranks", default="8,16,32,64")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run Phi^(n) for every mode --steps times (profiling target)")
     args = ap.parse_args(argv)
+    if args.r_sweep:
+        if args.workload == "c2":
+            args.workload = "c5"
+        if "--precision" not in (argv if argv is not None else sys.argv):
+            args.precision = "both"
+        run_r_sweep(args)
+        return
+    if args.precision == "both":
+        raise SystemExit("--precision both applies to --r-sweep only")
     if args.kernel_only:
         run_kernel_only(args)
         return
