@@ -19,11 +19,12 @@ namespace cpapr {
 namespace {
 constexpr int kThreads = sizeof(PHI_T) == 8 ? 128 : 256;
 // nonzeros per batch (U <= G when G > 1: after the reduce-scatter every lane
-// finishes one of them, so a nonzero costs G / U divisions).  FP64 at 16
+// finishes one of them, so a nonzero costs G / U divisions; one lane per
+// nonzero takes two at a time for memory-level parallelism).  FP64 at 16
 // ranks per lane has no registers to spare for a second batch entry.
 template <int RPL, int G>
 constexpr int unroll_for() {
-    if (sizeof(PHI_T) == 8) return RPL >= 16 ? (G >= 2 ? 2 : 1) : (G >= 4 ? 4 : (G >= 2 ? 2 : 1));
+    if (sizeof(PHI_T) == 8) return RPL >= 16 ? (G >= 2 ? 2 : 1) : (G >= 4 ? 4 : 2);
     return G >= 4 ? 4 : 2;
 }
 

@@ -261,7 +261,9 @@ cpapr_status autotune(cpapr_ctx *ctx) {
         for (int lanes = 1; lanes <= 32; lanes <<= 1) {
             if (!phi_config_supported((int)ctx->esize, ctx->N - 1, Rp, lanes)) continue;
             for (int tile : tiles) {
-                if (phi_smem_for((int)ctx->esize, ctx->N - 1, tile, Rp, lanes) > kMaxPhiSmem) continue;
+                // MTTKRP and the log-likelihood share the mode's tiles and stage every
+                // coordinate stream: keep room for two of their blocks per SM
+                if (phi_smem_for((int)ctx->esize, ctx->N - 1, tile, Rp, lanes) > kMaxPhiSmem / 2) continue;
                 for (int cand = 0; cand < 2 * npi; ++cand) {
                     const int red = cand % 2 ? CPAPR_REDUCE_SEGMENTED : CPAPR_REDUCE_ATOMIC;
                     const int pi = cand / 2;
