@@ -189,11 +189,13 @@ cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int redu
     L.lanes = lanes;
     L.reduction = reduction == CPAPR_REDUCE_ATOMIC ? CPAPR_REDUCE_ATOMIC : CPAPR_REDUCE_SEGMENTED;
     if (L.tile_nnz != tile || !L.row_first) CPAPR_TRY(build_tiles(ctx, n, tile));
-    // per-tile log-likelihood partials (mode 0)
-    if (n == 0) {
+    // per-tile log-likelihood partials (the sum runs along mode 0 or N-1)
+    if (L.ntiles > ctx->llpart_n || !ctx->llpart) {
         if (ctx->llpart) cudaFreeAsync(ctx->llpart, ctx->stream);
         ctx->llpart = nullptr;
+        ctx->llpart_n = 0;
         CPAPR_CUDA(ctx, cudaMallocAsync((void **)&ctx->llpart, (size_t)std::max(L.ntiles, 1) * 8, ctx->stream));
+        ctx->llpart_n = std::max(L.ntiles, 1);
     }
     if (ctx->graph_exec[n]) {
         cudaGraphExecDestroy(ctx->graph_exec[n]);
@@ -430,6 +432,7 @@ cpapr_status cpapr_set_model(cpapr_ctx *ctx, const double *lambda, const double 
     CPAPR_CUDA(ctx, cudaMemcpyAsync(flags, ctx->errflag, 16, cudaMemcpyDeviceToHost, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->k_total = 0;
+    ctx->pi_mode_built = -1;
     if (flags[2]) {
         ctx->model_set = false;
         return fail(ctx, CPAPR_E_VALUE, "factor entries must be finite and >= 0");
@@ -445,6 +448,7 @@ cpapr_status cpapr_init_random(cpapr_ctx *ctx, uint64_t seed) {
         CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->Phi[m], 0, (size_t)ctx->dims[m] * ctx->Rp * ctx->esize, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->k_total = 0;
+    ctx->pi_mode_built = -1;
     ctx->model_set = true;
     return CPAPR_OK;
 }
@@ -561,8 +565,7 @@ cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
     API_ENTER(ctx);
     if (!out) return fail(ctx, CPAPR_E_ARG, "out is NULL");
     if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
-    CPAPR_TRY(launch_scale_b(ctx, 0, ctx->B));
-    CPAPR_TRY(launch_loglik(ctx, ctx->B, ctx->scalars));
+    CPAPR_TRY(launch_loglik(ctx, ctx->scalars));
     CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(out, ctx->scalars, 8, cudaMemcpyDefault, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -442,7 +442,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
     cpapr_ctx *c0 = ctxs[0];
     const int N = c0->N;
     cudaStream_t s = c0->stream;
-    for (int i = 0; i < count; ++i) CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+    for (int i = 0; i < count; ++i) {
+        CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+        ctxs[i]->pi_mode_built = -1;  // the batched solve changes every factor
+    }
     // every tensor needs a rank class of the batched kernel and the segmented reduction
     for (int i = 0; i < count; ++i) {
         const int k = class_for<T>(ctxs[i]->Rp);

@@ -87,6 +87,8 @@ struct cpapr_ctx {
     void *carry = nullptr;
     int64_t carry_elems = 0;
     void *pibuf = nullptr;  // materialised Khatri-Rao rows of the current mode [nnz_pad x Rp]
+    int pi_mode_built = -1;  // mode whose rows pibuf holds, built from the current other factors (-1: none)
+    int64_t llpart_n = 0;    // capacity of llpart (tiles)
     double *colpart = nullptr;   // column-sum partials [kColParts x Rp]
     double *colsum = nullptr;    // per-mode column sums [N x Rp]
     double *llpart = nullptr;    // per-tile log-likelihood partials
@@ -168,7 +170,8 @@ int pi_fits(const cpapr_ctx *ctx);
 // bytes the staging barrier of the tile kernels expects beyond its copies (failure injection; 0 normally)
 uint32_t injected_stage_shortfall();
 // Sum of x log(m) over nonzeros, into llpart then *dst (device double).
-cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst);
+// log-likelihood sum of the current model (without the model total) into *dst (device)
+cpapr_status launch_loglik(cpapr_ctx *ctx, double *dst);
 // Rows of mode n without nonzeros: zero them in `out`; add their KKT term
 // (first inner iteration) after the S/B kernel.
 cpapr_status launch_zero_empty(cpapr_ctx *ctx, int n, void *out);

@@ -179,6 +179,8 @@ cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
     const int64_t rows = ctx->dims[n];
     const int Rp = ctx->Rp;
     const int parts = colsum_parts(rows, Rp);
+    // A^(n) changes: materialised rows of another mode that contain it go stale
+    if (n != ctx->pi_mode_built) ctx->pi_mode_built = -1;
     ProfScope ps(ctx, K_NORM);
     count_launch(ctx, 2);
     if (ctx->esize == 8) {

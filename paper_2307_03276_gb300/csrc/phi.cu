@@ -167,6 +167,7 @@ cpapr_status launch_pi_build(cpapr_ctx *ctx, int n) {
     const cudaError_t e = ctx->esize == 8 ? run_pi_build<double>(a, (double *)ctx->pibuf, ctx->stream)
                                           : run_pi_build<float>(a, (float *)ctx->pibuf, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "Pi build kernel");
+    ctx->pi_mode_built = n;
     return CPAPR_OK;
 }
 
@@ -232,14 +233,25 @@ __global__ void sum_parts_kernel(const double *__restrict__ part, int n, double 
     if (threadIdx.x == 0) *dst = sm[0];
 }
 
-cpapr_status launch_loglik(cpapr_ctx *ctx, const void *B0, double *dst) {
-    const ModeLayout &L = ctx->mode[0];
+// Log-likelihood sum over the nonzeros, x log m with m = <lambda o A^(n)[i_n], Pi>.
+// At the end of an outer iteration the materialised rows of the last mode
+// were built from the final factors of all the other modes, so in FP64 the
+// sum runs along that mode and streams them; otherwise it runs along mode 0
+// with the rows formed in place.  (The FP32 form keeps the gathered rows: its
+// underflow fallback recomputes products from the factors.)
+cpapr_status launch_loglik(cpapr_ctx *ctx, double *dst) {
+    const int N = ctx->N;
     if (ctx->nnz == 0) {
         CPAPR_CUDA(ctx, cudaMemsetAsync(dst, 0, 8, ctx->stream));
         return CPAPR_OK;
     }
-    PhiArgs a = make_args(ctx, 0, B0, nullptr, nullptr);
+    const bool use_pi = ctx->esize == 8 && ctx->pibuf && ctx->pi_mode_built == N - 1 && ctx->mode[N - 1].pi;
+    const int n = use_pi ? N - 1 : 0;
+    const ModeLayout &L = ctx->mode[n];
+    CPAPR_TRY(launch_scale_b(ctx, n, ctx->B));
+    PhiArgs a = make_args(ctx, n, ctx->B, nullptr, nullptr);
     a.atomic = 0;
+    if (use_pi) a.pi = ctx->pibuf;
     {
         ProfScope ps(ctx, K_LL);
         cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_LL);

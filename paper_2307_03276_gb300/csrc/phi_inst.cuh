@@ -47,6 +47,14 @@ cudaError_t run(const PhiArgs &a, cudaStream_t s) {
     else
         return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s);
 }
+// log-likelihood: FP64 can stream the materialised rows, FP32 always gathers
+template <int RPL, int G>
+cudaError_t run_ll(const PhiArgs &a, cudaStream_t s) {
+    if constexpr (sizeof(PHI_T) == 8) {
+        if (a.pi) return run<RPL, G, OP_LL, true>(a, s);
+    }
+    return run<RPL, G, OP_LL, false>(a, s);
+}
 }  // namespace
 
 // Returns cudaErrorInvalidValue when (rpl, lanes) has no instantiation.
@@ -57,7 +65,7 @@ cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s)
         if (op == OP_PHI)                                                                \
             return a.pi ? run<R_, G_, OP_PHI, true>(a, s) : run<R_, G_, OP_PHI, false>(a, s); \
         if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP, false>(a, s);                 \
-        return run<R_, G_, OP_LL, false>(a, s);                                          \
+        return run_ll<R_, G_>(a, s);                                                     \
     }
 #if PHI_IS_DOUBLE
     CPAPR_CASE(2, 1)

@@ -464,7 +464,8 @@ template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool 
 __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red,
                                               uint64_t *bar, uint32_t &phase) {
     static_assert(U == 1 || U == 2 || U == 4, "batches of 1, 2 or 4 nonzeros");
-    static_assert(!PI || OP == OP_PHI, "the materialised Pi serves Phi only");
+    static_assert(!PI || OP == OP_PHI || (OP == OP_LL && sizeof(T) == 8),
+                  "the materialised Pi serves Phi and the FP64 log-likelihood");
     constexpr int NG = THREADS / G;
     constexpr int NWARPS = THREADS / 32;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;

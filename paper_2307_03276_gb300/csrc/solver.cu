@@ -105,8 +105,7 @@ static cpapr_status enqueue_mode(cpapr_ctx *ctx, int n, double tol, int max_inne
 // Enqueues the log-likelihood of the current model and its copy to *host
 // (complete after the context's stream is synchronised).
 cpapr_status loglik_enqueue(cpapr_ctx *ctx, double *host) {
-    CPAPR_TRY(launch_scale_b(ctx, 0, ctx->B));
-    CPAPR_TRY(launch_loglik(ctx, ctx->B, ctx->scalars));
+    CPAPR_TRY(launch_loglik(ctx, ctx->scalars));
     CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(host, ctx->scalars, 8, cudaMemcpyDeviceToHost, ctx->stream));
     return CPAPR_OK;

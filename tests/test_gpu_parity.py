@@ -158,6 +158,24 @@ def test_loglik_matches_oracle(name, precision, tol):
     assert abs(got - want) <= tol * abs(want), (got, want)
 
 
+@pytest.mark.parametrize("name", ["c2s", "c3s", "c5s64"])
+def test_loglik_from_materialised_rows(name):
+    """After an outer iteration the last mode's materialised Khatri-Rao rows
+    were built from the final factors of the other modes; the FP64
+    log-likelihood then runs along that mode and streams them.  Both the
+    solver's value and a later cpapr_loglik match the oracle on the final model."""
+    T = case(name)
+    lam, fs = model_for(T, 15)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=cpapr.CPAPR_PI_MATERIALISED) as t:
+        t.set_model(lam, fs)
+        r = t.mu_solve(tol=1e-4, max_outer=1, max_inner=3)
+        got = t.loglik()
+        lam2, fs2 = t.get_model()
+    want = oracle.loglik(T.dims, T.idx, T.vals, lam2, fs2)
+    assert abs(got - want) <= 1e-11 * abs(want), (got, want)
+    assert abs(r["loglik"] - want) <= 1e-11 * abs(want), (r["loglik"], want)
+
+
 def test_explicit_b_with_epsilon_clamp():
     """A zero row of B clamps every denominator of that slice to eps (Algorithm 2)."""
     T = case("c1")
