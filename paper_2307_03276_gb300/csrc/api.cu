@@ -362,8 +362,12 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
     ctx->inner = (InnerState *)p;
     CR_TRY(dev_alloc(ctx, &p, (size_t)Rp * 8));
     ctx->lambda = (double *)p;
-    CR_TRY(dev_alloc(ctx, &p, (size_t)kColParts * Rp * 8));
+    CR_TRY(dev_alloc(ctx, &p, (size_t)nmodes * kColParts * Rp * 8));
     ctx->colpart = (double *)p;
+    CR_TRY(dev_alloc(ctx, &p, 16));
+    ctx->llcount = (unsigned int *)p;
+    if (cudaMemsetAsync(ctx->llcount, 0, 16, ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, CPAPR_E_CUDA, "memset"));
     CR_TRY(dev_alloc(ctx, &p, (size_t)nmodes * Rp * 8));
     ctx->colsum = (double *)p;
     CR_TRY(dev_alloc(ctx, &p, 64 * 8));
@@ -566,7 +570,6 @@ cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
     if (!out) return fail(ctx, CPAPR_E_ARG, "out is NULL");
     if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
     CPAPR_TRY(launch_loglik(ctx, ctx->scalars));
-    CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(out, ctx->scalars, 8, cudaMemcpyDefault, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return check_waits(ctx);

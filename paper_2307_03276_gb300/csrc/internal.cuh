@@ -89,7 +89,8 @@ struct cpapr_ctx {
     void *pibuf = nullptr;  // materialised Khatri-Rao rows of the current mode [nnz_pad x Rp]
     int pi_mode_built = -1;  // mode whose rows pibuf holds, built from the current other factors (-1: none)
     int64_t llpart_n = 0;    // capacity of llpart (tiles)
-    double *colpart = nullptr;   // column-sum partials [kColParts x Rp]
+    double *colpart = nullptr;   // column-sum partials [N x kColParts x Rp]
+    unsigned int *llcount = nullptr;  // last-block counter of the log-likelihood total (zero between launches)
     double *colsum = nullptr;    // per-mode column sums [N x Rp]
     double *llpart = nullptr;    // per-tile log-likelihood partials
     cpapr::InnerState *inner = nullptr;  // [N]
@@ -187,8 +188,8 @@ cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, Inn
                            unsigned long long cond_handle, int use_cond);
 cpapr_status launch_normalise(cpapr_ctx *ctx, int n);
 cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB);     // B = A^(n) diag(lambda)
-cpapr_status launch_colsums(cpapr_ctx *ctx);                          // colsum[m][r] for all m
-cpapr_status launch_ll_finish(cpapr_ctx *ctx, double *dst);           // dst -= sum_r lambda_r prod colsum
+// dst = sum of llpart[0..nll) - sum_r lambda_r prod_m colsum_m(r), one launch
+cpapr_status launch_ll_total(cpapr_ctx *ctx, const double *llpart, int nll, double *dst);
 cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed);
 cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst);   // R cols -> Rp cols, to T
 cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, double *dst); // Rp cols T -> R cols

@@ -220,50 +220,105 @@ cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB) {
 }
 
 // ---------------------------------------------------------------------------
-// column sums of every factor (for the log-likelihood's model total)
+// log-likelihood total: sum of the per-tile partials of sum x log m, minus the
+// model total sum_r lambda_r prod_m colsum_m(r), in one launch.  Blocks
+// [part0[m], part0[m+1]) take column partial sums of factor m; the last block
+// to finish (atomic election, no waiting) adds the partials of every column
+// in part order, the tile partials with a fixed tree, and writes the result.
 // ---------------------------------------------------------------------------
-__global__ void reduce_parts_kernel(const double *__restrict__ part, int nparts, int Rp, double *__restrict__ dst) {
-    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
-        double s = 0.0;
-        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * Rp + c];
-        dst[c] = s;
+struct LLTotalArgs {
+    const void *A[kMaxModes];
+    int64_t rows[kMaxModes];
+    int part0[kMaxModes + 1];  // first block of each mode; part0[N] = number of blocks
+    int N, Rp;
+    const double *lambda;
+    double *part;           // [blocks][Rp]
+    unsigned int *counter;  // zero between launches
+    const double *llpart;   // per-tile sums of x log m
+    int nll;
+    double *dst;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) ll_total_kernel(const LLTotalArgs a) {
+    __shared__ double sm[256];
+    __shared__ double cs[kMaxModes][256];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    int m = 0;
+    while (m + 1 < a.N && (int)blockIdx.x >= a.part0[m + 1]) ++m;
+    const int Rp = a.Rp;
+    const int p = (int)blockIdx.x - a.part0[m];
+    const int nparts = a.part0[m + 1] - a.part0[m];
+    const int c = tid % Rp, rl = tid / Rp, nrl = blockDim.x / Rp;
+    const T *M = reinterpret_cast<const T *>(a.A[m]);
+    double s = 0.0;
+    if (rl < nrl)
+        for (int64_t i = (int64_t)p * nrl + rl; i < a.rows[m]; i += (int64_t)nparts * nrl) s += (double)M[i * Rp + c];
+    sm[tid] = s;
+    __syncthreads();
+    if (tid < Rp) {
+        double t = 0.0;
+        for (int k = 0; k < nrl; ++k) t += sm[k * Rp + tid];
+        a.part[(int64_t)blockIdx.x * Rp + tid] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // sum of the tile partials: per-thread strided sums, then a tree
+    double v = 0.0;
+    for (int i = tid; i < a.nll; i += 256) v += __ldcg(a.llpart + i);
+    sm[tid] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) sm[tid] += sm[tid + w];
+        __syncthreads();
+    }
+    // column sums of every factor, partials in order
+    if (tid < Rp)
+        for (int mm = 0; mm < a.N; ++mm) {
+            double t = 0.0;
+            for (int q = a.part0[mm]; q < a.part0[mm + 1]; ++q) t += __ldcg(a.part + (int64_t)q * Rp + tid);
+            cs[mm][tid] = t;
+        }
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int cc = 0; cc < Rp; ++cc) {
+            double pr = a.lambda[cc];
+            for (int mm = 0; mm < a.N; ++mm) pr *= cs[mm][cc];
+            tot += pr;
+        }
+        *a.dst = sm[0] - tot;
+        *a.counter = 0u;  // ready for the next launch
     }
 }
 
-cpapr_status launch_colsums(cpapr_ctx *ctx) {
-    const int Rp = ctx->Rp;
+cpapr_status launch_ll_total(cpapr_ctx *ctx, const double *llpart, int nll, double *dst) {
+    LLTotalArgs a{};
+    int blocks = 0;
     for (int m = 0; m < ctx->N; ++m) {
-        const int64_t rows = ctx->dims[m];
-        const int parts = colsum_parts(rows, Rp);
-        if (ctx->esize == 8)
-            colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->A[m], rows, Rp,
-                                                                           ctx->colpart);
-        else
-            colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->A[m], rows, Rp,
-                                                                          ctx->colpart);
-        reduce_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->colpart, parts, Rp, ctx->colsum + (int64_t)m * Rp);
-        count_launch(ctx, 2);
-        CPAPR_CUDA(ctx, cudaGetLastError());
+        a.A[m] = ctx->A[m];
+        a.rows[m] = ctx->dims[m];
+        a.part0[m] = blocks;
+        blocks += colsum_parts(ctx->dims[m], ctx->Rp);
     }
-    return CPAPR_OK;
-}
-
-// dst -= sum_r lambda_r prod_m colsum_m(r): the model's total over all entries
-__global__ void ll_finish_kernel(const double *__restrict__ lambda, const double *__restrict__ colsum, int N, int Rp,
-                                 double *__restrict__ dst) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double tot = 0.0;
-    for (int c = 0; c < Rp; ++c) {
-        double p = lambda[c];
-        for (int m = 0; m < N; ++m) p *= colsum[(int64_t)m * Rp + c];
-        tot += p;
-    }
-    *dst = *dst - tot;
-}
-
-cpapr_status launch_ll_finish(cpapr_ctx *ctx, double *dst) {
-    CPAPR_TRY(launch_colsums(ctx));
-    ll_finish_kernel<<<1, 32, 0, ctx->stream>>>(ctx->lambda, ctx->colsum, ctx->N, ctx->Rp, dst);
+    a.part0[ctx->N] = blocks;
+    a.N = ctx->N;
+    a.Rp = ctx->Rp;
+    a.lambda = ctx->lambda;
+    a.part = ctx->colpart;
+    a.counter = ctx->llcount;
+    a.llpart = llpart;
+    a.nll = nll;
+    a.dst = dst;
+    if (ctx->esize == 8)
+        ll_total_kernel<double><<<blocks, 256, 0, ctx->stream>>>(a);
+    else
+        ll_total_kernel<float><<<blocks, 256, 0, ctx->stream>>>(a);
     count_launch(ctx);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;

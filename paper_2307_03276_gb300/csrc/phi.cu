@@ -219,20 +219,6 @@ cpapr_status launch_phi_given_carry(cpapr_ctx *ctx, int n, const void *B, void *
     return CPAPR_OK;
 }
 
-__global__ void sum_parts_kernel(const double *__restrict__ part, int n, double *__restrict__ dst) {
-    // one block, fixed order: per-thread strided sums, then a tree
-    __shared__ double sm[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += 256) s += part[i];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *dst = sm[0];
-}
-
 // Log-likelihood sum over the nonzeros, x log m with m = <lambda o A^(n)[i_n], Pi>.
 // At the end of an outer iteration the materialised rows of the last mode
 // were built from the final factors of all the other modes, so in FP64 the
@@ -241,10 +227,7 @@ __global__ void sum_parts_kernel(const double *__restrict__ part, int n, double 
 // underflow fallback recomputes products from the factors.)
 cpapr_status launch_loglik(cpapr_ctx *ctx, double *dst) {
     const int N = ctx->N;
-    if (ctx->nnz == 0) {
-        CPAPR_CUDA(ctx, cudaMemsetAsync(dst, 0, 8, ctx->stream));
-        return CPAPR_OK;
-    }
+    if (ctx->nnz == 0) return launch_ll_total(ctx, ctx->llpart, 0, dst);  // the model total alone
     const bool use_pi = ctx->esize == 8 && ctx->pibuf && ctx->pi_mode_built == N - 1 && ctx->mode[N - 1].pi;
     const int n = use_pi ? N - 1 : 0;
     const ModeLayout &L = ctx->mode[n];
@@ -256,9 +239,8 @@ cpapr_status launch_loglik(cpapr_ctx *ctx, double *dst) {
         ProfScope ps(ctx, K_LL);
         cudaError_t e = dispatch(ctx, a, ctx->Rp / L.lanes, L.lanes, OP_LL);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "log-likelihood kernel");
-        sum_parts_kernel<<<1, 256, 0, ctx->stream>>>(ctx->llpart, L.ntiles, dst);
-        count_launch(ctx, 2);
-        CPAPR_CUDA(ctx, cudaGetLastError());
+        count_launch(ctx);
+        CPAPR_TRY(launch_ll_total(ctx, ctx->llpart, L.ntiles, dst));
     }
     return CPAPR_OK;
 }

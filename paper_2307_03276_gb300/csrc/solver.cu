@@ -106,7 +106,6 @@ static cpapr_status enqueue_mode(cpapr_ctx *ctx, int n, double tol, int max_inne
 // (complete after the context's stream is synchronised).
 cpapr_status loglik_enqueue(cpapr_ctx *ctx, double *host) {
     CPAPR_TRY(launch_loglik(ctx, ctx->scalars));
-    CPAPR_TRY(launch_ll_finish(ctx, ctx->scalars));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(host, ctx->scalars, 8, cudaMemcpyDeviceToHost, ctx->stream));
     return CPAPR_OK;
 }
