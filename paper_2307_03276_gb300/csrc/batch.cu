@@ -87,13 +87,30 @@ template <typename T> __host__ __device__ constexpr int batch_threads() { return
 // keep one float4 per lane, like the single-tensor kernel's four-block case)
 template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 4; }
 
-template <typename T, int NM1, int K>
+template <typename T, int NM1, int K, bool PI = false>
 __device__ __forceinline__ bool run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red, uint64_t *bar,
                                           uint32_t &phase) {
     constexpr int RPL = Classes<T>::rpl[K];
     constexpr int G = Classes<T>::g[K];
-    return phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>()>(a, tile, smem, red,
-                                                                                               bar, phase);
+    return phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>(), PI>(a, tile, smem,
+                                                                                                   red, bar, phase);
+}
+
+// One item's tile with the tensor's rank class; FP64 tensors with
+// materialised Khatri-Rao rows (a.pi set) stream them.
+template <typename T, int NM1, bool PI>
+__device__ __forceinline__ bool run_item(const PhiArgs &a, int cfg, int tile, unsigned char *smem, double *red,
+                                         uint64_t *bar, uint32_t &phase) {
+    switch (cfg) {
+        case 0: return run_class<T, NM1, 0, PI>(a, tile, smem, red, bar, phase);
+        case 1: return run_class<T, NM1, 1, PI>(a, tile, smem, red, bar, phase);
+        case 2: return run_class<T, NM1, 2, PI>(a, tile, smem, red, bar, phase);
+        case 3: return run_class<T, NM1, 3, PI>(a, tile, smem, red, bar, phase);
+        default:
+            if constexpr (Classes<T>::n > 4)
+                return run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0), PI>(a, tile, smem, red, bar, phase);
+            return true;
+    }
 }
 
 template <typename T, int NM1>
@@ -116,16 +133,13 @@ __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) bat
         if (it >= nitems) break;
         const int2 w = items[it];
         const PhiArgs a = desc[w.x].a;
-        switch (desc[w.x].cfg) {
-            case 0: ok = run_class<T, NM1, 0>(a, w.y, smem_raw, red, &bar, phase); break;
-            case 1: ok = run_class<T, NM1, 1>(a, w.y, smem_raw, red, &bar, phase); break;
-            case 2: ok = run_class<T, NM1, 2>(a, w.y, smem_raw, red, &bar, phase); break;
-            case 3: ok = run_class<T, NM1, 3>(a, w.y, smem_raw, red, &bar, phase); break;
-            default:
-                if constexpr (Classes<T>::n > 4)
-                    ok = run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0)>(a, w.y, smem_raw, red, &bar, phase);
-                break;
+        if constexpr (sizeof(T) == 8) {
+            if (a.pi) {
+                ok = run_item<T, NM1, true>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
+                continue;
+            }
         }
+        ok = run_item<T, NM1, false>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
     }
     // the last block out resets the work counter for the next launch
     if (threadIdx.x == 0) {
@@ -137,6 +151,24 @@ __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) bat
             __threadfence();
         }
     }
+}
+
+constexpr int64_t kPiChunk = 1 << 16;  // 16-byte vectors of Khatri-Rao rows per build item
+
+// Materialised Khatri-Rao rows of every tensor that streams them, for mode n:
+// one block per (tensor, chunk of kPiChunk vectors) item; skipped tensors
+// (converged or finished) keep their rows.
+template <typename T, int NM1>
+__global__ void __launch_bounds__(256) batch_pi_build_kernel(const BatchTensor *__restrict__ desc,
+                                                             const int2 *__restrict__ items,
+                                                             const int32_t *__restrict__ flags) {
+    const int2 w = items[blockIdx.x];
+    if (flags[2 * w.x]) return;
+    const PhiArgs &a = desc[w.x].a;
+    const int64_t total = a.nnz * (a.Rp / Vec16<T>::n);
+    const int64_t e0 = (int64_t)w.y * kPiChunk;
+    pi_build_range<T, NM1>(a, reinterpret_cast<T *>(const_cast<void *>(a.pi)), e0 + threadIdx.x,
+                           min(e0 + kPiChunk, total), (int64_t)blockDim.x);
 }
 
 // flags[2t] = skip (converged or finished), flags[2t+1] = apply the shift S
@@ -317,6 +349,8 @@ struct ModePlan {
     cudaGraphExec_t exec = nullptr;
     int body_kernels = 0;
     size_t smem = 0;  // dynamic shared memory of the Phi launch (largest tile of the batch)
+    int2 *pitems = nullptr;  // (tensor, chunk) items of the batched Khatri-Rao row build
+    int npitems = 0;
 };
 
 struct Plan {
@@ -353,6 +387,17 @@ cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ct
         case 4: return go(batch_phi_kernel<T, 4>);
         default: return go(batch_phi_kernel<T, 0>);
     }
+}
+
+template <typename T>
+cudaError_t launch_pi_batch(const ModePlan &mp, int nm1, const int32_t *flags, cudaStream_t s) {
+    switch (nm1) {
+        case 2: batch_pi_build_kernel<T, 2><<<mp.npitems, 256, 0, s>>>(mp.desc, mp.pitems, flags); break;
+        case 3: batch_pi_build_kernel<T, 3><<<mp.npitems, 256, 0, s>>>(mp.desc, mp.pitems, flags); break;
+        case 4: batch_pi_build_kernel<T, 4><<<mp.npitems, 256, 0, s>>>(mp.desc, mp.pitems, flags); break;
+        default: batch_pi_build_kernel<T, 0><<<mp.npitems, 256, 0, s>>>(mp.desc, mp.pitems, flags); break;
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -515,7 +560,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
     for (int n = 0; n < N; ++n) {
         ModePlan &mp = P.modes[n];
         std::vector<BatchTensor> desc(count);
-        std::vector<int2> tiles, chunks, echunks;
+        std::vector<int2> tiles, chunks, echunks, pitems;
         for (int i = 0; i < count; ++i) {
             cpapr_ctx *c = ctxs[i];
             const ModeLayout &L = c->mode[n];
@@ -550,6 +595,12 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.llpart = c->llpart;
             a.err = c->errflag + 3;
             a.stage_extra = injected_stage_shortfall();
+            // FP64 tensors whose mode n materialises its Khatri-Rao rows stream them here too
+            if (sizeof(T) == 8 && L.pi && c->pibuf && c->nnz > 0) {
+                a.pi = c->pibuf;
+                const int64_t vecs = c->nnz * (c->Rp / Vec16<T>::n);
+                for (int64_t q = 0; q < ceil_div(vecs, kPiChunk); ++q) pitems.push_back(make_int2(i, (int)q));
+            }
             d.cfg = class_for<T>(c->Rp);
             d.rp = c->Rp;
             d.rows = c->dims[n];
@@ -586,6 +637,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         BT_CUDA(dalloc((void **)&mp.echunks, echunks.size() * sizeof(int2)));
         if (!echunks.empty())
             BT_CUDA(cudaMemcpy(mp.echunks, echunks.data(), echunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        mp.npitems = (int)pitems.size();
+        BT_CUDA(dalloc((void **)&mp.pitems, pitems.size() * sizeof(int2)));
+        if (!pitems.empty())
+            BT_CUDA(cudaMemcpy(mp.pitems, pitems.data(), pitems.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.desc, desc.data(), desc.size() * sizeof(BatchTensor), cudaMemcpyHostToDevice));
         if (!tiles.empty())
             BT_CUDA(cudaMemcpy(mp.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -634,6 +689,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             if (mp.nechunks > 0) {
                 batch_empty_kkt_kernel<T><<<mp.nechunks, 256, 0, s>>>(mp.desc, mp.echunks, P.flags);
                 BT_CUDA(cudaGetLastError());
+            }
+            if (mp.npitems > 0) {
+                BT_CUDA(launch_pi_batch<T>(mp, N - 1, P.flags, s));
+                c0->launches += 1;
             }
             if (graph) {
                 BT_CUDA(cudaGraphLaunch(mp.exec, s));

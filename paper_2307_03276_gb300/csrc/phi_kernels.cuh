@@ -904,17 +904,18 @@ __global__ void __launch_bounds__(THREADS, 4) phi_tile_kernel_occ4(const PhiArgs
 // m != n, for every nonzero p in mode-n order.  The products are taken in the
 // same order as the fused tile kernel forms them, so a Phi from the
 // materialised Pi equals the fused one bit for bit.  One thread per 16-byte
-// vector of a row; rows are written with evict-first stores (read once per
-// inner iteration, they are not worth keeping in L2).
+// vector of a row (elements e0, e0 + step, ... below e1); rows are written
+// with evict-first stores (read once per inner iteration, they are not worth
+// keeping in L2).
 template <typename T, int NM1>
-__global__ void __launch_bounds__(256) pi_build_kernel(const PhiArgs a, T *__restrict__ pi) {
+__device__ __forceinline__ void pi_build_range(const PhiArgs &a, T *__restrict__ pi, int64_t e0, int64_t e1,
+                                               int64_t step) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::n;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
     const int nm1 = NM1 > 0 ? NM1 : a.nm1;
     const int vpr = a.Rp / VN;  // vectors per row
-    const int64_t total = a.nnz * vpr;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = e0; e < e1; e += step) {
         const int64_t p = e / vpr;
         const int c = (int)(e - p * vpr) * VN;
         V x = __ldg(reinterpret_cast<const V *>(reinterpret_cast<const T *>(a.A[0]) +
@@ -937,6 +938,13 @@ __global__ void __launch_bounds__(256) pi_build_kernel(const PhiArgs a, T *__res
         }
         __stcs(reinterpret_cast<V *>(pi + p * a.Rp + c), x);
     }
+}
+
+template <typename T, int NM1>
+__global__ void __launch_bounds__(256) pi_build_kernel(const PhiArgs a, T *__restrict__ pi) {
+    const int64_t total = a.nnz * (a.Rp / Vec16<T>::n);
+    pi_build_range<T, NM1>(a, pi, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, total,
+                           (int64_t)gridDim.x * blockDim.x);
 }
 
 // FP32 with one float4 per lane runs at four blocks per SM
