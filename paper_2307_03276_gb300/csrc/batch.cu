@@ -83,9 +83,10 @@ __host__ __device__ constexpr int batch_unroll() {
 }
 
 template <typename T> __host__ __device__ constexpr int batch_threads() { return sizeof(T) == 8 ? 128 : 256; }
-// resident blocks per SM the registers are held to (the FP32 classes all
-// keep one float4 per lane, like the single-tensor kernel's four-block case)
-template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 2 : 4; }
+// resident blocks per SM the registers are held to (measured on GB300): the
+// FP32 classes all keep one float4 per lane, like the single-tensor kernel's
+// four-block case; every FP64 class fits three blocks (168 registers)
+template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 3 : 4; }
 
 template <typename T, int NM1, int K, bool PI = false>
 __device__ __forceinline__ bool run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red, uint64_t *bar,
