@@ -57,6 +57,8 @@ L2_GATHER_GBS = 7450.0
 # (workload, dtype, Pi form, lanes per mode, tile per mode); a run in any other configuration reports
 # traffic null, and an entry is dropped when its kernel changes.
 NCU_TRAFFIC = {
+    ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
+        ([2.8338e9, 2.8274e9, 2.7655e9], "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"),
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
         ([202.1e6, 201.0e6, 197.4e6], "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"),
 }
