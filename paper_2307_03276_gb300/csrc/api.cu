@@ -58,11 +58,50 @@ static bool injected_alloc_failure() {
     return k > 0 && ++calls == k;
 }
 
+// Device memory of every context comes from one stream-ordered pool per
+// device owned by the library.  The pool keeps up to a quarter of the
+// device's memory cached after frees, so contexts created and destroyed in a
+// loop (a new tensor per request) do not pay for cudaMalloc / cudaFree each
+// time; memory above that is returned to the driver at synchronisation.
+static cudaMemPool_t device_pool(int dev) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        uint64_t keep = (uint64_t)totalb / 4;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaGetLastError();
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+cudaError_t lib_malloc_raw(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaMallocAsync(p, std::max<size_t>(bytes, 16), s);
+    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, s);
+}
+
 cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (injected_alloc_failure()) return fail(ctx, CPAPR_E_NOMEM, "injected allocation failure (CPAPR_FAULT_ALLOC_AT)");
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    cudaError_t e = lib_malloc(p, bytes, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation");
     ctx->allocs.push_back(*p);
     ctx->device_bytes += (int64_t)bytes;
     return CPAPR_OK;
@@ -194,7 +233,7 @@ cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int redu
         if (ctx->llpart) cudaFreeAsync(ctx->llpart, ctx->stream);
         ctx->llpart = nullptr;
         ctx->llpart_n = 0;
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&ctx->llpart, (size_t)std::max(L.ntiles, 1) * 8, ctx->stream));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&ctx->llpart, (size_t)std::max(L.ntiles, 1) * 8, ctx->stream));
         ctx->llpart_n = std::max(L.ntiles, 1);
     }
     if (ctx->graph_exec[n]) {
@@ -279,15 +318,16 @@ void cpapr_destroy(cpapr_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (int n = 0; n < ctx->N; ++n) {
         ModeLayout &L = ctx->mode[n];
-        if (L.row_first) cudaFree(L.row_first);
-        if (L.split) cudaFree(L.split);
-        if (L.tsplit) cudaFree(L.tsplit);
-        if (L.splitcnt) cudaFree(L.splitcnt);
+        if (L.row_first) cudaFreeAsync(L.row_first, ctx->stream);
+        if (L.split) cudaFreeAsync(L.split, ctx->stream);
+        if (L.tsplit) cudaFreeAsync(L.tsplit, ctx->stream);
+        if (L.splitcnt) cudaFreeAsync(L.splitcnt, ctx->stream);
         if (ctx->graph_exec[n]) cudaGraphExecDestroy(ctx->graph_exec[n]);
     }
-    if (ctx->carry) cudaFree(ctx->carry);
-    if (ctx->llpart) cudaFree(ctx->llpart);
-    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->carry) cudaFreeAsync(ctx->carry, ctx->stream);
+    if (ctx->llpart) cudaFreeAsync(ctx->llpart, ctx->stream);
+    for (void *p : ctx->allocs) cudaFreeAsync(p, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);

@@ -105,7 +105,7 @@ cpapr_status exclusive_scan_u32(cpapr_ctx *ctx, uint32_t *data, int64_t n, uint3
     int64_t nb = ceil_div(n, kScanTile);
     uint32_t *bs = nullptr;
     if (nb > 1) {
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&bs, nb * 4, ctx->stream));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&bs, nb * 4, ctx->stream));
         scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(data, n, bs);
         count_launch(ctx);
         CPAPR_CUDA(ctx, cudaGetLastError());
@@ -220,7 +220,7 @@ static cpapr_status radix_sort(cpapr_ctx *ctx, uint32_t *keys, uint32_t *vals, u
     if (n <= 1 || bits <= 0) return CPAPR_OK;
     int ntiles = (int)ceil_div(n, kRsTile);
     uint32_t *counts = nullptr;
-    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&counts, (size_t)256 * ntiles * 4, ctx->stream));
+    CPAPR_CUDA(ctx, lib_malloc((void **)&counts, (size_t)256 * ntiles * 4, ctx->stream));
     uint32_t *ka = keys, *va = vals, *kb = tk, *vb = tv;
     int passes = (bits + 7) / 8;
     for (int ps = 0; ps < passes; ++ps) {
@@ -325,10 +325,10 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
 
     const int64_t nb = std::max<int64_t>(nnz, 1);
     BL_CUDA(cudaMemsetAsync(ctx->errflag, 0, 16, s));
-    BL_CUDA(cudaMallocAsync((void **)&stage, nb * 8, s));
-    BL_CUDA(cudaMallocAsync((void **)&vals, nb * 8, s));
+    BL_CUDA(lib_malloc((void **)&stage, nb * 8, s));
+    BL_CUDA(lib_malloc((void **)&vals, nb * 8, s));
     for (int m = 0; m < N; ++m) {
-        BL_CUDA(cudaMallocAsync((void **)&idx32[m], nb * 4, s));
+        BL_CUDA(lib_malloc((void **)&idx32[m], nb * 4, s));
         if (nnz > 0) {
             BL_CUDA(cudaMemcpyAsync(stage, idx_in[m], nnz * 8, cudaMemcpyDefault, s));
             narrow_check_kernel<<<grid_for(nnz), 256, 0, s>>>(stage, nnz, ctx->dims[m], idx32[m], ctx->errflag);
@@ -356,10 +356,10 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
     cudaFreeAsync(stage, s);
     stage = nullptr;
 
-    BL_CUDA(cudaMallocAsync((void **)&keys, nb * 4, s));
-    BL_CUDA(cudaMallocAsync((void **)&perm, nb * 4, s));
-    BL_CUDA(cudaMallocAsync((void **)&tk, nb * 4, s));
-    BL_CUDA(cudaMallocAsync((void **)&tv, nb * 4, s));
+    BL_CUDA(lib_malloc((void **)&keys, nb * 4, s));
+    BL_CUDA(lib_malloc((void **)&perm, nb * 4, s));
+    BL_CUDA(lib_malloc((void **)&tk, nb * 4, s));
+    BL_CUDA(lib_malloc((void **)&tv, nb * 4, s));
 
     for (int n = 0; n < N; ++n) {
         ModeLayout &L = ctx->mode[n];
@@ -412,7 +412,7 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
     for (int n = 0; n < N; ++n) {
         ModeLayout &L = ctx->mode[n];
         uint32_t *flag = nullptr;
-        BL_CUDA(cudaMallocAsync((void **)&flag, (size_t)(L.In + 1) * 4, s));
+        BL_CUDA(lib_malloc((void **)&flag, (size_t)(L.In + 1) * 4, s));
         empty_flags_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flag);
         BL_CUDA(cudaGetLastError());
         cpapr_status st = exclusive_scan_u32(ctx, flag, L.In, flag + L.In);
@@ -521,13 +521,13 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     L.ntiles = (int32_t)ceil_div(ctx->nnz, tile_nnz);
     L.nsplit = 0;
     const int nt = L.ntiles;
-    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.row_first, (size_t)std::max(nt, 1) * 4, s));
+    CPAPR_CUDA(ctx, lib_malloc((void **)&L.row_first, (size_t)std::max(nt, 1) * 4, s));
     count_launch(ctx, nt >= 2 ? 3 : 1);
     tile_rows_kernel<<<(unsigned)ceil_div(std::max(nt, 1), 256), 256, 0, s>>>(L.seg, L.In, tile_nnz, nt, L.row_first);
     CPAPR_CUDA(ctx, cudaGetLastError());
     if (nt >= 2) {
         uint32_t *flag = nullptr, *dtot = nullptr;
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&flag, (size_t)nt * 4 + 4, s));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&flag, (size_t)nt * 4 + 4, s));
         dtot = flag + nt;
         split_flags_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag);
         CPAPR_CUDA(ctx, cudaGetLastError());
@@ -536,28 +536,28 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
         CPAPR_CUDA(ctx, cudaMemcpyAsync(&total, dtot, 4, cudaMemcpyDeviceToHost, s));
         CPAPR_CUDA(ctx, cudaStreamSynchronize(s));
         L.nsplit = (int32_t)total;
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, (size_t)std::max<int>(L.nsplit, 1) * 12, s));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&L.split, (size_t)std::max<int>(L.nsplit, 1) * 12, s));
         split_write_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag, L.split);
         CPAPR_CUDA(ctx, cudaGetLastError());
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.tsplit, (size_t)nt * 8, s));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&L.tsplit, (size_t)nt * 8, s));
         tile_split_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(L.seg, L.row_first, tile_nnz, nt, flag, dtot,
                                                                       L.tsplit);
         count_launch(ctx);
         CPAPR_CUDA(ctx, cudaGetLastError());
         CPAPR_CUDA(ctx, cudaFreeAsync(flag, s));
     } else {
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.split, 12, s));
-        CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.tsplit, (size_t)std::max(nt, 1) * 8, s));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&L.split, 12, s));
+        CPAPR_CUDA(ctx, lib_malloc((void **)&L.tsplit, (size_t)std::max(nt, 1) * 8, s));
         CPAPR_CUDA(ctx, cudaMemsetAsync(L.tsplit, 0xff, (size_t)std::max(nt, 1) * 8, s));
     }
-    CPAPR_CUDA(ctx, cudaMallocAsync((void **)&L.splitcnt, (size_t)std::max(L.nsplit, 1) * 4, s));
+    CPAPR_CUDA(ctx, lib_malloc((void **)&L.splitcnt, (size_t)std::max(L.nsplit, 1) * 4, s));
     CPAPR_CUDA(ctx, cudaMemsetAsync(L.splitcnt, 0, (size_t)std::max(L.nsplit, 1) * 4, s));
     // the carry buffer holds two partial rows per tile
     int64_t need = (int64_t)2 * std::max(nt, 1) * ctx->Rp;
     if (need > ctx->carry_elems) {
         if (ctx->carry) cudaFreeAsync(ctx->carry, s);
         ctx->carry = nullptr;
-        CPAPR_CUDA(ctx, cudaMallocAsync(&ctx->carry, (size_t)need * ctx->esize, s));
+        CPAPR_CUDA(ctx, lib_malloc(&ctx->carry, (size_t)need * ctx->esize, s));
         ctx->carry_elems = need;
     }
     CPAPR_CUDA(ctx, cudaStreamSynchronize(s));

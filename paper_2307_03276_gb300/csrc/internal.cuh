@@ -137,6 +137,11 @@ cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what);
     } while (0)
 
 cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes);
+// stream-ordered allocation from the library's memory pool of the current device
+cudaError_t lib_malloc_raw(void **p, size_t bytes, cudaStream_t s);
+template <typename T> inline cudaError_t lib_malloc(T **p, size_t bytes, cudaStream_t s) {
+    return lib_malloc_raw(reinterpret_cast<void **>(p), bytes, s);
+}
 
 // Counts kernel launches; launches recorded while a stream capture is active
 // are not counted here (graph replays are counted from the iterations run).
