@@ -14,11 +14,13 @@
 //   2. per mode n: stable LSD radix sort of (i_n, position) with 8-bit digits
 //      (per-tile digit histograms, an exclusive scan, and a stable scatter
 //      that ranks equal digits with warp match/ballot);
-//   3. seg[i] = first sorted position of row i (I_n + 1 offsets);
+//   3. seg[i] = first sorted position of row i (I_n + 1 offsets) and the
+//      sorted row ids themselves (the tile kernels stage them with the tile);
 //   4. gather the other modes' coordinates and the values in sorted order;
 //   5. tile tables: tiles of tile_nnz consecutive sorted nonzeros, the row
-//      holding each tile's first nonzero, the first row starting in each
-//      tile, and the list of rows that span more than one tile.
+//      holding each tile's first nonzero, the rows that span more than one
+//      tile with, per tile, the split its head and tail partials belong to,
+//      and one counter per split.
 #include <cuda_runtime.h>
 
 #include <algorithm>

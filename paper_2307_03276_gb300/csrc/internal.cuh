@@ -163,7 +163,7 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz);
 
 // ---- Phi family (phi.cu) -----------------------------------------------------
 enum PhiOp { OP_PHI = 0, OP_MTTKRP = 1, OP_LL = 2 };
-// Launches the tile kernel (+ fix-up) for mode n writing `out` (I_n x Rp).
+// Launches the tile kernel for mode n writing `out` (I_n x Rp).
 // B: I_n x Rp of the working type (ignored for MTTKRP).  inner: state whose
 // done flag / kkt slot the kernels use (may be null for a one-off Phi).
 cpapr_status launch_phi(cpapr_ctx *ctx, int n, PhiOp op, const void *B, void *out, InnerState *inner);

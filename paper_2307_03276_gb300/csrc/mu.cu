@@ -3,6 +3,8 @@
 //   B <- (A^(n) + S) Lambda            sb_kernel
 //   B <- B * Phi unless KKT passed     update_kernel (also the loop bookkeeping)
 //   lambda <- e^T B; A <- B Lambda^-1  colsum_partial_kernel + normalise_kernel
+//   log-likelihood total               ll_total_kernel (column sums, tile
+//                                      partials and the model total at once)
 // and the model I/O helpers.  All reductions that decide or normalise run in
 // FP64 whatever the working precision.
 #include <cuda_runtime.h>

@@ -5,9 +5,9 @@
 // budget), or whose calls sit in a loop that must not block on the driver's
 // allocator, cannot let the library call cudaMalloc/cudaFree per call.
 // cpapr_phi itself allocates nothing either, but the Phi kernel's scratch
-// (the per-tile partial rows that the boundary fix-up adds up) lives in a
-// buffer sized at cpapr_create time and grown with cudaMallocAsync when the
-// tiling changes.  This variant takes that scratch from a fixed array in
+// (the per-tile partial rows of rows that span tiles, which the last tile to
+// arrive adds up) lives in a buffer sized at cpapr_create time and grown
+// with a stream-ordered allocation when the tiling changes.  This variant takes that scratch from a fixed array in
 // device memory that the library image carries, so the call itself only
 // launches kernels and copies between device buffers.
 //
@@ -93,8 +93,10 @@ extern "C" cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const do
             CPAPR_TRY(upload_matrix(ctx, B, ctx->dims[mode], ctx->B));
         else
             CPAPR_TRY(launch_scale_b(ctx, mode, ctx->B));
-        // the per-tile partials land in the fixed scratch; every slot the
-        // fix-up reads is written earlier in this call, so nothing is cleared
+        // the per-tile partials land in the fixed scratch; every slot a
+        // finishing tile reads is written earlier in this launch, so nothing
+        // is cleared (the materialised rows, if the mode uses them, live in
+        // the context's buffer and are rebuilt for this call)
         CPAPR_TRY(launch_pi_build(ctx, mode));
         CPAPR_TRY(launch_phi_given_carry(ctx, mode, ctx->B, ctx->outbuf, scratch));
         CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));

@@ -2,13 +2,14 @@
 //
 // Per outer iteration and mode n, everything stays on the device:
 //   sb_kernel                    B <- (A^(n) + S) Lambda, inner state reset
-//   inner loop (<= max_inner):   Phi tile kernel (+ fix-up) with the KKT
-//                                violation folded in, then update_kernel
+//   pi_build_kernel              Khatri-Rao rows of mode n (if materialised)
+//   inner loop (<= max_inner):   Phi tile kernel with the KKT violation
+//                                folded in, then update_kernel
 //                                (B <- B * Phi unless the check passed)
 //   normalise                    lambda <- e^T B, A^(n) <- B Lambda^-1
 // The inner loop runs either as plain stream launches whose kernels return
 // at once after the check passed, or as a CUDA graph holding a conditional
-// WHILE node whose body is {Phi, fix-up, update}; update_kernel clears the
+// WHILE node whose body is {Phi, update}; update_kernel clears the
 // loop condition on the device, so no host round trip decides the exit.
 // The host reads the per-mode inner states back once per outer iteration to
 // test outer convergence (every mode passed its check at the first inner

@@ -91,7 +91,8 @@ def test_phi_fp64_matches_oracle(name, reduction, pi_mode):
 @pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s64"])
 @pytest.mark.parametrize("tile", [64, 320, 4096])
 def test_phi_fp64_tile_sizes(name, tile):
-    """Small tiles cut many rows across tiles and groups (fix-up path), large ones few."""
+    """Small tiles cut many rows across tiles and groups (rows finished by the
+    last tile to arrive), large ones few."""
     T = case(name)
     lam, fs = model_for(T, 9)
     with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tile_nnz=tile) as t:
