@@ -610,6 +610,81 @@ def run_r_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+PPA_WINDOW = 16
+
+
+def ppa_phi_ms(cp, T, lam, fs, precision, pi_mode, reduction, modes, reps):
+    """Average Phi (and Pi build) launch time over `modes`, heuristic tiling."""
+    with cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, profile=1, use_graph=0,
+                   pi_mode=pi_mode, reduction=reduction) as t:
+        t.set_model(lam, fs)
+        for n in modes:
+            t.phi(n)
+        t.kernel_stats(cp.K_PHI, reset=True)
+        t.kernel_stats(cp.K_PI, reset=True)
+        for _ in range(reps):
+            for n in modes:
+                t.phi(n)
+        pl, pms = t.kernel_stats(cp.K_PHI)
+        bl, bms = t.kernel_stats(cp.K_PI)
+        info = t.info()
+    return {"phi_ms": pms / max(pl, 1), "pi_build_ms": (bms / bl) if bl else 0.0,
+            "tile_nnz": list(info.tile_nnz)[:T.nmodes], "rank_lanes": list(info.rank_lanes)[:T.nmodes]}
+
+
+def run_ppa(args):
+    """Pressure-point probes after the paper's performance analysis (Section
+    "Pressure Point Analysis"), on GB300.
+
+    Data reuse: Phi^(0) of a 3-way 1e5 x 1e5 x 1e3 tensor with 1e7 nonzeros
+    and R = 32 whose mode-0 rows are uniform, once with modes 1 and 2 uniform
+    over their full range and once with them confined to their first
+    PPA_WINDOW rows (every factor row gathered stays cache-resident; the
+    tensor, its streams and B/Phi keep their sizes).  The paper hard-codes
+    the gathered row instead; here the input carries the access pattern, so
+    the kernels run unchanged and their results stay exact.
+
+    Atomics: the paper swaps the atomic row update for an unsynchronised one
+    (wrong results, timing only).  The segmented reduction here is the
+    non-atomic form that stays correct, so the probe times the 3-way Zipf
+    workload with reduction = atomic against reduction = segmented."""
+    import torch
+    from paper_2307_03276_gb300 import build, cpapr as cp, synth
+    torch.cuda.set_device(0)
+    build.build()
+    reps = max(1, args.steps)
+    c2 = synth.C2
+    out = {"probe": "pressure_points", "reuse": [], "atomic": []}
+    layouts = {"full": (("uniform",),) * 3,
+               "window": (("uniform",), ("window", PPA_WINDOW), ("window", PPA_WINDOW))}
+    forms = [(cp.CPAPR_FP64, cp.CPAPR_PI_FUSED), (cp.CPAPR_FP64, cp.CPAPR_PI_MATERIALISED),
+             (cp.CPAPR_FP32, cp.CPAPR_PI_FUSED), (cp.CPAPR_FP32, cp.CPAPR_PI_MATERIALISED)]
+    for name, modes in layouts.items():
+        spec = synth.TensorSpec(c2.dims, c2.nnz, c2.rank, modes, c2.values, 1102,
+                                f"ppa_3way_1e5x1e5x1e3_1e7_r32_{name}")
+        T = synth.generate(spec)
+        fs = synth.random_factors(T.dims, T.rank, 5)
+        lam = np.ones(T.rank)
+        for prec, pim in forms:
+            r = ppa_phi_ms(cp, T, lam, fs, prec, pim, cp.CPAPR_REDUCE_SEGMENTED, [0], reps)
+            r.update({"tensor": name, "window_rows": PPA_WINDOW if name == "window" else None,
+                      "dtype": "f64" if prec == cp.CPAPR_FP64 else "f32",
+                      "pi": "fused" if pim == cp.CPAPR_PI_FUSED else "materialised", "mode": 0})
+            out["reuse"].append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+        del T
+    T, lam, fs = make_workload("c2")
+    for prec, pim in [(cp.CPAPR_FP64, cp.CPAPR_PI_MATERIALISED), (cp.CPAPR_FP32, cp.CPAPR_PI_FUSED)]:
+        for red, rname in [(cp.CPAPR_REDUCE_SEGMENTED, "segmented"), (cp.CPAPR_REDUCE_ATOMIC, "atomic")]:
+            r = ppa_phi_ms(cp, T, lam, fs, prec, pim, red, list(range(T.nmodes)), reps)
+            r.update({"workload": T.name, "dtype": "f64" if prec == cp.CPAPR_FP64 else "f32",
+                      "pi": "fused" if pim == cp.CPAPR_PI_FUSED else "materialised", "reduction": rname,
+                      "phi_nnz_per_s": T.nnz / (r["phi_ms"] / 1e3)})
+            out["atomic"].append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores, on bounded samples of the same workload."""
     world, rank, _ = dist_env()
@@ -661,7 +736,12 @@ def main(argv=None):
     ap.add_argument("--ranks", default="8,16,32,64")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run Phi^(n) for every mode --steps times (profiling target)")
+    ap.add_argument("--ppa", action="store_true",
+                    help="pressure-point probes: factor-row reuse and atomic vs segmented reduction")
     args = ap.parse_args(argv)
+    if args.ppa:
+        run_ppa(args)
+        return
     if args.r_sweep:
         if args.workload == "c2":
             args.workload = "c5"

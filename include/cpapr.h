@@ -94,6 +94,14 @@ enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
  *             device memory; else fused.
  *             MTTKRP, the log-likelihood and the batched solver always form
  *             the rows in place.
+ *  l2_persist 1 = mark the factor matrices (held in one allocation) as
+ *             persisting in L2 for the kernels that gather factor rows (Phi,
+ *             MTTKRP, log-likelihood, the Khatri-Rao build): an access-policy
+ *             window over them on each such launch, with the process's
+ *             persisting-L2 set-aside raised to cover it (up to the device
+ *             maximum; never lowered; persisting lines are returned to normal
+ *             when the context is destroyed).  0 = off (default).  Ignored
+ *             on devices without persisting L2.
  */
 typedef struct {
     int32_t precision;
@@ -109,7 +117,8 @@ typedef struct {
     int32_t autotune;
     int32_t profile;
     int32_t pi_mode;
-    int32_t reserved[4];
+    int32_t l2_persist;
+    int32_t reserved[3];
 } cpapr_options;
 
 void cpapr_default_options(cpapr_options *opt);
@@ -275,6 +284,7 @@ typedef struct {
     int32_t pi_mode[CPAPR_MAX_MODES];     /* CPAPR_PI_FUSED or CPAPR_PI_MATERIALISED, per mode */
     int64_t device_bytes;  /* device memory held by the context */
     int64_t kernel_launches; /* kernels this context has launched (graph replays counted per kernel) */
+    int64_t l2_window_bytes; /* bytes of the persisting-L2 window over the factors (0: none) */
 } cpapr_info;
 
 cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info);

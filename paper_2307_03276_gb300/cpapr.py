@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("kappa_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile_nnz", ctypes.c_int32), ("rank_lanes", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("pi_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("pi_mode", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Result(ctypes.Structure):
@@ -60,7 +60,7 @@ class Info(ctypes.Structure):
                 ("reduction", ctypes.c_int32 * MAX_MODES), ("ntiles", ctypes.c_int32 * MAX_MODES),
                 ("nsplit", ctypes.c_int32 * MAX_MODES), ("pi_mode", ctypes.c_int32 * MAX_MODES),
                 ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("l2_window_bytes", ctypes.c_int64)]
 
 
 _lib = None

@@ -282,6 +282,31 @@ int pi_auto(const cpapr_ctx *ctx) { return (ctx->esize == 8 || ctx->N >= 4) ? pi
 
 cpapr_status autotune(cpapr_ctx *ctx);
 
+// Access-policy window over the factor block: hits persist in the set-aside
+// part of L2, raised (never lowered) to cover the window where the device
+// allows; the hit ratio scales the window down to the set-aside.
+cpapr_status configure_l2_window(cpapr_ctx *ctx) {
+    int max_persist = 0, max_window = 0;
+    CPAPR_CUDA(ctx, cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
+    CPAPR_CUDA(ctx, cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
+    if (max_persist <= 0 || max_window <= 0 || ctx->factor_bytes == 0) return CPAPR_OK;
+    const size_t window = std::min(ctx->factor_bytes, (size_t)max_window);
+    size_t setaside = 0;
+    CPAPR_CUDA(ctx, cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize));
+    const size_t want = std::min(window, (size_t)max_persist);
+    if (setaside < want) {
+        CPAPR_CUDA(ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+        CPAPR_CUDA(ctx, cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize));
+    }
+    if (setaside == 0) return CPAPR_OK;
+    ctx->l2win.base_ptr = ctx->factor_block;
+    ctx->l2win.num_bytes = window;
+    ctx->l2win.hitRatio = (float)std::min(1.0, (double)setaside / (double)window);
+    ctx->l2win.hitProp = cudaAccessPropertyPersisting;
+    ctx->l2win.missProp = cudaAccessPropertyStreaming;
+    return CPAPR_OK;
+}
+
 }  // namespace cpapr
 
 using namespace cpapr;
@@ -312,6 +337,7 @@ const char *cpapr_last_error(const cpapr_ctx *ctx) {
     return ctx->err.empty() ? "no error" : ctx->err.c_str();
 }
 
+
 void cpapr_destroy(cpapr_ctx *ctx) {
     if (!ctx) return;
     batch_forget(ctx);
@@ -328,6 +354,8 @@ void cpapr_destroy(cpapr_ctx *ctx) {
     if (ctx->llpart) cudaFreeAsync(ctx->llpart, ctx->stream);
     for (void *p : ctx->allocs) cudaFreeAsync(p, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
+    // lines this context marked persisting go back to normal priority
+    if (ctx->l2win.num_bytes) cudaCtxResetPersistingL2Cache();
     for (auto &p : ctx->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);
@@ -361,6 +389,7 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
         return fail(nullptr, CPAPR_E_ARG, "rank_lanes must be 0 or a power of two <= 32");
     if (o.tile_nnz != 0 && (o.tile_nnz < 64 || o.tile_nnz > (1 << 20) || o.tile_nnz % 4))
         return fail(nullptr, CPAPR_E_ARG, "tile_nnz must be 0 or a multiple of 4 in [64, 2^20]");
+    if (o.l2_persist != 0 && o.l2_persist != 1) return fail(nullptr, CPAPR_E_ARG, "l2_persist must be 0 or 1");
 
     cpapr_ctx *ctx = new (std::nothrow) cpapr_ctx();
     if (!ctx) return fail(nullptr, CPAPR_E_NOMEM, "host allocation failed");
@@ -417,9 +446,15 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
 
     CR_TRY(build_layouts(ctx, idx, vals));
 
+    // the factor matrices share one allocation (each start 256-byte aligned)
+    // so that one access-policy window can cover all of them
+    size_t fofs[CPAPR_MAX_MODES + 1] = {};
+    for (int m = 0; m < nmodes; ++m)
+        fofs[m + 1] = fofs[m] + (((size_t)dims[m] * Rp * ctx->esize + 255) & ~(size_t)255);
+    CR_TRY(dev_alloc(ctx, &ctx->factor_block, fofs[nmodes]));
+    ctx->factor_bytes = fofs[nmodes];
     for (int m = 0; m < nmodes; ++m) {
-        CR_TRY(dev_alloc(ctx, &p, (size_t)dims[m] * Rp * ctx->esize));
-        ctx->A[m] = p;
+        ctx->A[m] = (char *)ctx->factor_block + fofs[m];
         CR_TRY(dev_alloc(ctx, &p, (size_t)dims[m] * Rp * ctx->esize));
         ctx->Phi[m] = p;
         if (cudaMemsetAsync(ctx->A[m], 0, (size_t)dims[m] * Rp * ctx->esize, ctx->stream) != cudaSuccess ||
@@ -432,6 +467,8 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
     ctx->outbuf = p;
     CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * 8));
     ctx->stage = (double *)p;
+
+    if (o.l2_persist) CR_TRY(configure_l2_window(ctx));
 
     for (int n = 0; n < nmodes; ++n) {
         int lanes, tile, red;
@@ -660,6 +697,7 @@ cpapr_status cpapr_get_info(const cpapr_ctx *ctx, cpapr_info *info) {
     }
     info->device_bytes = ctx->device_bytes;
     info->kernel_launches = ctx->launches;
+    info->l2_window_bytes = (int64_t)ctx->l2win.num_bytes;
     return CPAPR_OK;
 }
 

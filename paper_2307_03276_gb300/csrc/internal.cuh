@@ -79,7 +79,10 @@ struct cpapr_ctx {
     cpapr::ModeLayout mode[CPAPR_MAX_MODES];
     // model
     double *lambda = nullptr;
-    void *A[CPAPR_MAX_MODES] = {};
+    void *A[CPAPR_MAX_MODES] = {};   // views into factor_block
+    void *factor_block = nullptr;    // all factor matrices, one allocation
+    size_t factor_bytes = 0;
+    cudaAccessPolicyWindow l2win{};  // persisting-L2 window over factor_block (num_bytes 0: none)
     void *B = nullptr;
     void *outbuf = nullptr;  // Phi / MTTKRP output of the one-off calls (Imax x Rp)
     void *Phi[CPAPR_MAX_MODES] = {};
@@ -137,6 +140,12 @@ cpapr_status cuda_fail(cpapr_ctx *ctx, cudaError_t e, const char *what);
     } while (0)
 
 cpapr_status dev_alloc(cpapr_ctx *ctx, void **p, size_t bytes);
+// persisting-L2 access-policy window over the factor matrices (l2_persist)
+cpapr_status configure_l2_window(cpapr_ctx *ctx);
+// the window for launches that gather factor rows, or null
+inline const cudaAccessPolicyWindow *l2_window(const cpapr_ctx *ctx) {
+    return ctx->l2win.num_bytes ? &ctx->l2win : nullptr;
+}
 // stream-ordered allocation from the library's memory pool of the current device
 cudaError_t lib_malloc_raw(void **p, size_t bytes, cudaStream_t s);
 template <typename T> inline cudaError_t lib_malloc(T **p, size_t bytes, cudaStream_t s) {

@@ -8,14 +8,14 @@
 
 namespace cpapr {
 
-cudaError_t launch_phi_f64_n0(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f64_n2(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f64_n3(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f64_n4(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f32_n0(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f32_n2(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f32_n3(const PhiArgs &, int, int, int, cudaStream_t);
-cudaError_t launch_phi_f32_n4(const PhiArgs &, int, int, int, cudaStream_t);
+cudaError_t launch_phi_f64_n0(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f64_n2(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f64_n3(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f64_n4(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f32_n0(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f32_n2(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f32_n3(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
+cudaError_t launch_phi_f32_n4(const PhiArgs &, int, int, int, cudaStream_t, const cudaAccessPolicyWindow *);
 
 bool phi_config_supported(int esize, int nm1, int rp, int lanes) {
     (void)nm1;
@@ -43,19 +43,21 @@ size_t phi_smem_for(int esize, int nm1, int tile, int rp, int lanes) {
 
 static cudaError_t dispatch(const cpapr_ctx *ctx, const PhiArgs &a, int rpl, int lanes, int op) {
     const int nm1 = ctx->N - 1;
+    // Phi over materialised rows gathers no factor rows: no window
+    const cudaAccessPolicyWindow *win = (op == OP_PHI && a.pi) ? nullptr : l2_window(ctx);
     if (ctx->esize == 8) {
         switch (nm1) {
-            case 2: return launch_phi_f64_n2(a, rpl, lanes, op, ctx->stream);
-            case 3: return launch_phi_f64_n3(a, rpl, lanes, op, ctx->stream);
-            case 4: return launch_phi_f64_n4(a, rpl, lanes, op, ctx->stream);
-            default: return launch_phi_f64_n0(a, rpl, lanes, op, ctx->stream);
+            case 2: return launch_phi_f64_n2(a, rpl, lanes, op, ctx->stream, win);
+            case 3: return launch_phi_f64_n3(a, rpl, lanes, op, ctx->stream, win);
+            case 4: return launch_phi_f64_n4(a, rpl, lanes, op, ctx->stream, win);
+            default: return launch_phi_f64_n0(a, rpl, lanes, op, ctx->stream, win);
         }
     }
     switch (nm1) {
-        case 2: return launch_phi_f32_n2(a, rpl, lanes, op, ctx->stream);
-        case 3: return launch_phi_f32_n3(a, rpl, lanes, op, ctx->stream);
-        case 4: return launch_phi_f32_n4(a, rpl, lanes, op, ctx->stream);
-        default: return launch_phi_f32_n0(a, rpl, lanes, op, ctx->stream);
+        case 2: return launch_phi_f32_n2(a, rpl, lanes, op, ctx->stream, win);
+        case 3: return launch_phi_f32_n3(a, rpl, lanes, op, ctx->stream, win);
+        case 4: return launch_phi_f32_n4(a, rpl, lanes, op, ctx->stream, win);
+        default: return launch_phi_f32_n0(a, rpl, lanes, op, ctx->stream, win);
     }
 }
 
@@ -145,17 +147,35 @@ cpapr_status launch_empty_kkt(cpapr_ctx *ctx, int n, const void *B, InnerState *
     return CPAPR_OK;
 }
 
+template <typename T, int NM1>
+static cudaError_t launch_pi_kernel(const PhiArgs &a, T *pi, unsigned grid, cudaStream_t s,
+                                    const cudaAccessPolicyWindow *win) {
+    if (!win) {
+        pi_build_kernel<T, NM1><<<grid, 256, 0, s>>>(a, pi);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *win;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pi_build_kernel<T, NM1>, a, pi);
+}
+
 template <typename T>
-static cudaError_t run_pi_build(const PhiArgs &a, T *pi, cudaStream_t s) {
+static cudaError_t run_pi_build(const PhiArgs &a, T *pi, cudaStream_t s, const cudaAccessPolicyWindow *win) {
     const int64_t total = a.nnz * (a.Rp / Vec16<T>::n);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 152 * 16));
     switch (a.nm1) {
-        case 2: pi_build_kernel<T, 2><<<grid, 256, 0, s>>>(a, pi); break;
-        case 3: pi_build_kernel<T, 3><<<grid, 256, 0, s>>>(a, pi); break;
-        case 4: pi_build_kernel<T, 4><<<grid, 256, 0, s>>>(a, pi); break;
-        default: pi_build_kernel<T, 0><<<grid, 256, 0, s>>>(a, pi); break;
+        case 2: return launch_pi_kernel<T, 2>(a, pi, grid, s, win);
+        case 3: return launch_pi_kernel<T, 3>(a, pi, grid, s, win);
+        case 4: return launch_pi_kernel<T, 4>(a, pi, grid, s, win);
+        default: return launch_pi_kernel<T, 0>(a, pi, grid, s, win);
     }
-    return cudaGetLastError();
 }
 
 cpapr_status launch_pi_build(cpapr_ctx *ctx, int n) {
@@ -164,8 +184,8 @@ cpapr_status launch_pi_build(cpapr_ctx *ctx, int n) {
     PhiArgs a = make_args(ctx, n, nullptr, nullptr, nullptr);
     ProfScope ps(ctx, K_PI);
     count_launch(ctx);
-    const cudaError_t e = ctx->esize == 8 ? run_pi_build<double>(a, (double *)ctx->pibuf, ctx->stream)
-                                          : run_pi_build<float>(a, (float *)ctx->pibuf, ctx->stream);
+    const cudaError_t e = ctx->esize == 8 ? run_pi_build<double>(a, (double *)ctx->pibuf, ctx->stream, l2_window(ctx))
+                                          : run_pi_build<float>(a, (float *)ctx->pibuf, ctx->stream, l2_window(ctx));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "Pi build kernel");
     ctx->pi_mode_built = n;
     return CPAPR_OK;

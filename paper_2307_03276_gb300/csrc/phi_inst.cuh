@@ -28,44 +28,59 @@ constexpr int unroll_for() {
     return G >= 4 ? 4 : 2;
 }
 
+// win: persisting-L2 window for the launch, or null for a plain launch
 template <int RPL, typename K>
-cudaError_t launch(K k, const PhiArgs &a, cudaStream_t s) {
+cudaError_t launch(K k, const PhiArgs &a, cudaStream_t s, const cudaAccessPolicyWindow *win) {
     const size_t smem = phi_smem_bytes(a.T, a.pi ? 0 : a.nm1, (int)sizeof(PHI_T), kThreads, RPL);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (a.ntiles > 0) k<<<a.ntiles, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.ntiles <= 0) return cudaGetLastError();
+    if (!win) {
+        k<<<a.ntiles, kThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *win;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.ntiles);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 template <int RPL, int G, int OP, bool PI>
-cudaError_t run(const PhiArgs &a, cudaStream_t s) {
+cudaError_t run(const PhiArgs &a, cudaStream_t s, const cudaAccessPolicyWindow *win) {
     constexpr int U = unroll_for<RPL, G>();
     if constexpr (phi_occ4<PHI_T, RPL>())
-        return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s);
+        return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
     else
-        return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s);
+        return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
 }
 // log-likelihood: FP64 can stream the materialised rows, FP32 always gathers
 template <int RPL, int G>
-cudaError_t run_ll(const PhiArgs &a, cudaStream_t s) {
+cudaError_t run_ll(const PhiArgs &a, cudaStream_t s, const cudaAccessPolicyWindow *win) {
     if constexpr (sizeof(PHI_T) == 8) {
-        if (a.pi) return run<RPL, G, OP_LL, true>(a, s);
+        if (a.pi) return run<RPL, G, OP_LL, true>(a, s, win);
     }
-    return run<RPL, G, OP_LL, false>(a, s);
+    return run<RPL, G, OP_LL, false>(a, s, win);
 }
 }  // namespace
 
 // Returns cudaErrorInvalidValue when (rpl, lanes) has no instantiation.
 // Phi reads the materialised Khatri-Rao rows when a.pi is set.
-cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s) {
-#define CPAPR_CASE(R_, G_)                                                               \
-    if (rpl == R_ && lanes == G_) {                                                      \
-        if (op == OP_PHI)                                                                \
-            return a.pi ? run<R_, G_, OP_PHI, true>(a, s) : run<R_, G_, OP_PHI, false>(a, s); \
-        if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP, false>(a, s);                 \
-        return run_ll<R_, G_>(a, s);                                                     \
+cudaError_t PHI_FN(const PhiArgs &a, int rpl, int lanes, int op, cudaStream_t s, const cudaAccessPolicyWindow *win) {
+#define CPAPR_CASE(R_, G_)                                                                          \
+    if (rpl == R_ && lanes == G_) {                                                                 \
+        if (op == OP_PHI)                                                                           \
+            return a.pi ? run<R_, G_, OP_PHI, true>(a, s, win) : run<R_, G_, OP_PHI, false>(a, s, win); \
+        if (op == OP_MTTKRP) return run<R_, G_, OP_MTTKRP, false>(a, s, win);                      \
+        return run_ll<R_, G_>(a, s, win);                                                           \
     }
 #if PHI_IS_DOUBLE
     CPAPR_CASE(2, 1)

@@ -128,7 +128,7 @@ class TensorSpec:
     dims: tuple
     nnz: int
     rank: int
-    modes: tuple            # per mode: ("zipf", alpha) or ("uniform",)
+    modes: tuple            # per mode: ("zipf", alpha), ("uniform",) or ("window", W)
     values: tuple           # ("poisson1", mu) -> Poisson(mu)+1, ("geometric", p) -> {1,2,..}
     seed: int
     name: str = ""
@@ -181,6 +181,12 @@ def _draw_mode(spec: TensorSpec, m: int, base: np.uint64, start: int, n: int, ca
     u = uniform01(base, start, n)
     if kind[0] == "uniform":
         return np.minimum((u * dim).astype(np.int64), dim - 1)
+    if kind[0] == "window":
+        # uniform over the first W rows of a mode that keeps its full size:
+        # the factor rows read through this mode stay cache-resident (the
+        # "data reuse" pressure point of the paper's performance analysis)
+        w = min(int(kind[1]), dim)
+        return np.minimum((u * w).astype(np.int64), w - 1)
     if kind[0] == "zipf":
         # P(k) proportional to (k + 1)^-alpha, sampled with an alias table
         key = ("zipf", m)

@@ -54,15 +54,16 @@ def test_ctypes_structs_match_c_layout(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "cpapr.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(cpapr_options),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(cpapr_options),"
         " offsetof(cpapr_options, stream), offsetof(cpapr_options, profile), sizeof(cpapr_result),"
-        " offsetof(cpapr_result, loglik), sizeof(cpapr_info), offsetof(cpapr_info, device_bytes));return 0;}\n")
+        " offsetof(cpapr_result, loglik), sizeof(cpapr_info), offsetof(cpapr_info, device_bytes),"
+        " offsetof(cpapr_options, l2_persist), offsetof(cpapr_info, l2_window_bytes));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(cpapr.Options), cpapr.Options.stream.offset, cpapr.Options.profile.offset,
             ctypes.sizeof(cpapr.Result), cpapr.Result.loglik.offset, ctypes.sizeof(cpapr.Info),
-            cpapr.Info.device_bytes.offset]
+            cpapr.Info.device_bytes.offset, cpapr.Options.l2_persist.offset, cpapr.Info.l2_window_bytes.offset]
     assert got == want
 
 
@@ -83,4 +84,7 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert e.value.status == 1
     with pytest.raises(cpapr.CpaprError) as e:
         cpapr.cpapr_create([3, 3, 3], idx, vals, 2, cpapr.cpapr_default_options(rank_lanes=3))
+    assert e.value.status == 1
+    with pytest.raises(cpapr.CpaprError) as e:
+        cpapr.cpapr_create([3, 3, 3], idx, vals, 2, cpapr.cpapr_default_options(l2_persist=2))
     assert e.value.status == 1

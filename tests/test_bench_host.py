@@ -3,6 +3,7 @@
 import os
 import socket
 
+import numpy as np
 import pytest
 
 import bench
@@ -61,3 +62,18 @@ def test_aggregate_two_ranks_gloo():
         assert p.exitcode == 0
     for rank, u, s in got:
         assert u == 300.0 and s == 1.5
+
+
+def test_window_mode_distribution():
+    """A ("window", W) mode draws uniformly from the first W rows of a mode
+    that keeps its full size (the data-reuse pressure-point input)."""
+    from paper_2307_03276_gb300 import synth
+    spec = synth.TensorSpec((500, 400, 300), 20_000, 4, (("uniform",), ("window", 8), ("window", 500)),
+                            ("poisson1", 1.0), 7, "w")
+    T = synth.generate(spec)
+    assert T.dims == (500, 400, 300) and T.nnz == 20_000
+    assert T.idx[1].min() == 0 and T.idx[1].max() == 7
+    assert T.idx[2].max() == 299          # a window wider than the mode is the whole mode
+    counts = np.bincount(T.idx[1], minlength=8)
+    assert counts.min() > 0.8 * T.nnz / 8  # near-uniform over the window
+    assert len({tuple(c) for c in T.idx.T}) == T.nnz

@@ -525,3 +525,37 @@ def test_invalid_inputs_are_errors_not_faults():
             t.phi(3)
         assert e.value.status == 1
         t.phi(2)
+
+
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+@pytest.mark.parametrize("pi_mode", PI_MODES)
+def test_l2_persist_window_changes_no_result(precision, pi_mode):
+    """The persisting-L2 window over the factor matrices only changes cache
+    priorities: Phi, MTTKRP, the log-likelihood and a short MU solve are
+    bit-identical with and without it, and the info block reports the window
+    (the factors fit the device's window on this workload)."""
+    T = case("c2s")
+    lam, fs = model_for(T, 15)
+    out = {}
+    for l2 in (0, 1):
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, pi_mode=pi_mode, l2_persist=l2) as t:
+            info = t.info()
+            if l2:
+                factor_bytes = sum(d * info.rank_padded * (8 if precision == cpapr.CPAPR_FP64 else 4) for d in T.dims)
+                assert factor_bytes <= info.l2_window_bytes <= factor_bytes + 256 * T.nmodes
+            else:
+                assert info.l2_window_bytes == 0
+            t.set_model(lam, fs)
+            phis = [t.phi(n) for n in range(T.nmodes)]
+            mtt = [t.mttkrp(n) for n in range(T.nmodes)]
+            ll = t.loglik()
+            r = t.mu_solve(tol=1e-4, max_outer=2, max_inner=3)
+            out[l2] = (phis, mtt, ll, r, t.get_model(), t.loglik())
+    a, b = out[0], out[1]
+    for x, y in zip(a[0] + a[1], b[0] + b[1]):
+        assert np.array_equal(x, y)
+    assert a[2] == b[2] and a[5] == b[5]
+    assert a[3]["total_inner"] == b[3]["total_inner"]
+    assert np.array_equal(a[4][0], b[4][0])
+    for x, y in zip(a[4][1], b[4][1]):
+        assert np.array_equal(x, y)
