@@ -283,11 +283,15 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__
     }
 }
 
+// Column partials per chunk; the last chunk of each tensor to finish (an
+// atomic count per tensor, no waiting) adds them in chunk order into lambda.
 template <typename T>
 __global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchTensor *__restrict__ desc,
                                                            const int2 *__restrict__ chunks,
-                                                           const int32_t *__restrict__ flags) {
+                                                           const int32_t *__restrict__ flags,
+                                                           unsigned int *__restrict__ chunk_count) {
     __shared__ double sm[256];
+    __shared__ bool last;
     const int2 w = chunks[blockIdx.x];
     const BatchTensor &d = desc[w.x];
     if (flags[2 * w.x]) return;
@@ -306,32 +310,47 @@ __global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchTensor *__
         for (int k = 0; k < nrl; ++k) t += sm[k * Rp + threadIdx.x];
         d.colpart[(int64_t)w.y * Rp + threadIdx.x] = t;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&chunk_count[w.x], 1u) == (unsigned)d.nchunks - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c2 = threadIdx.x; c2 < Rp; c2 += blockDim.x) {
+        double t = 0.0;
+        for (int p = 0; p < d.nchunks; ++p) t += __ldcg(d.colpart + (int64_t)p * Rp + c2);
+        d.lambda[c2] = t;
+    }
+    if (threadIdx.x == 0) chunk_count[w.x] = 0;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) batch_scale_kernel(const BatchTensor *__restrict__ desc,
                                                           const int2 *__restrict__ chunks,
                                                           const int32_t *__restrict__ flags) {
-    __shared__ double lam[256];
+    __shared__ double lam[256], inv[256];
     const int2 w = chunks[blockIdx.x];
     const BatchTensor &d = desc[w.x];
     if (flags[2 * w.x]) return;
     const int Rp = d.rp;
+    // one reciprocal per column (no overflow: lambda >= 2^-1000, else a plain
+    // division); lambda = 0 marks an all-zero column, whose A stays
     for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
-        double s = 0.0;
-        for (int p = 0; p < d.nchunks; ++p) s += d.colpart[(int64_t)p * Rp + c];
-        lam[c] = s;
+        const double l = d.lambda[c];
+        lam[c] = l;
+        inv[c] = l >= 0x1p-1000 ? 1.0 / l : 0.0;
     }
     __syncthreads();
-    if (w.y == 0)
-        for (int c = threadIdx.x; c < Rp; c += blockDim.x) d.lambda[c] = lam[c];
     const int64_t r0 = (int64_t)w.y * kChunkRows;
     const int64_t r1 = min(r0 + kChunkRows, d.rows);
     const T *B = reinterpret_cast<const T *>(d.a.B);
     T *A = reinterpret_cast<T *>(d.A);
     for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
-        const double l = lam[e % Rp];
-        if (l > 0.0) A[e] = (T)((double)B[e] / l);
+        const int c = (int)(e & (Rp - 1));  // Rp is a power of two
+        const double l = lam[c];
+        if (l > 0.0) A[e] = (T)(inv[c] != 0.0 ? (double)B[e] * inv[c] : (double)B[e] / l);
     }
 }
 
@@ -357,11 +376,13 @@ struct ModePlan {
 struct Plan {
     std::vector<ModePlan> modes;
     BatchCtl *ctl = nullptr;
-    unsigned int *chunk_count = nullptr;
+    unsigned int *chunk_count = nullptr;  // per tensor: chunks of the update done (zero between launches)
+    unsigned int *col_count = nullptr;    // per tensor: chunks of the column sums done (zero between launches)
     double *colpart = nullptr;
     int32_t *flags = nullptr;
     InnerState **state_ptrs = nullptr;
     InnerState *states = nullptr;
+    double *ll = nullptr;  // [count] final log-likelihoods
     std::vector<void *> owned;
     // what the plan was built for (it is reused while these match)
     std::vector<cpapr_ctx *> key;
@@ -546,11 +567,14 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
     BT_CUDA(dalloc((void **)&P.colpart, (size_t)colpart_total * 8));
     BT_CUDA(dalloc((void **)&P.ctl, sizeof(BatchCtl)));
     BT_CUDA(dalloc((void **)&P.chunk_count, (size_t)count * 4));
+    BT_CUDA(dalloc((void **)&P.col_count, (size_t)count * 4));
     BT_CUDA(dalloc((void **)&P.flags, (size_t)count * 8));
     BT_CUDA(dalloc((void **)&P.state_ptrs, (size_t)count * N * sizeof(InnerState *)));
     BT_CUDA(dalloc((void **)&P.states, (size_t)count * N * sizeof(InnerState)));
+    BT_CUDA(dalloc((void **)&P.ll, (size_t)count * sizeof(double)));
     BT_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(BatchCtl), s));
     BT_CUDA(cudaMemsetAsync(P.chunk_count, 0, (size_t)count * 4, s));
+    BT_CUDA(cudaMemsetAsync(P.col_count, 0, (size_t)count * 4, s));
     {
         std::vector<InnerState *> sp((size_t)count * N);
         for (int i = 0; i < count; ++i)
@@ -702,7 +726,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
                     st = enqueue_inner_body<T>(c0, P, n, tol, max_inner, 0ull, 0, grid);
                 if (st != CPAPR_OK) break;
             }
-            batch_colsum_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
+            batch_colsum_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags, P.col_count);
             batch_scale_kernel<T><<<mp.nchunks, 256, 0, s>>>(mp.desc, mp.chunks, P.flags);
             BT_CUDA(cudaGetLastError());
         }
@@ -746,7 +770,8 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         return st;
     }
     // final log-likelihoods: every tensor on its own stream after the batch
-    // stream's work, one synchronisation for all
+    // stream's work, into one device array that the batch stream copies back
+    // once all of them are done (one host wait for the whole batch)
     std::vector<double> ll(count, 0.0);
     cudaEvent_t done_ev = nullptr;
     CPAPR_CUDA(c0, cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
@@ -757,10 +782,18 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         return cuda_fail(c0, e, "batch log-likelihood ordering");
     }
     cpapr_status lst = CPAPR_OK;
-    for (int i = 0; i < count && lst == CPAPR_OK; ++i) lst = loglik_enqueue(ctxs[i], &ll[i]);
-    for (int i = 0; i < count; ++i) {
-        cudaError_t se = cudaStreamSynchronize(ctxs[i]->stream);
-        if (se != cudaSuccess && lst == CPAPR_OK) lst = cuda_fail(ctxs[i], se, "cudaStreamSynchronize");
+    for (int i = 0; i < count && lst == CPAPR_OK; ++i) {
+        lst = launch_loglik(ctxs[i], P.ll + i);
+        if (lst != CPAPR_OK) break;
+        // the batch stream waits for this tensor's sum (the event is re-recorded per tensor)
+        e = cudaEventRecord(done_ev, ctxs[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done_ev, 0);
+        if (e != cudaSuccess) lst = cuda_fail(ctxs[i], e, "batch log-likelihood ordering");
+    }
+    if (lst == CPAPR_OK) {
+        e = cudaMemcpyAsync(ll.data(), P.ll, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) lst = cuda_fail(c0, e, "batch log-likelihood copy");
     }
     cudaEventDestroy(done_ev);
     if (lst != CPAPR_OK) return lst;

@@ -93,7 +93,7 @@ struct cpapr_ctx {
     int pi_mode_built = -1;  // mode whose rows pibuf holds, built from the current other factors (-1: none)
     int64_t llpart_n = 0;    // capacity of llpart (tiles)
     double *colpart = nullptr;   // column-sum partials [N x kColParts x Rp]
-    unsigned int *llcount = nullptr;  // last-block counter of the log-likelihood total (zero between launches)
+    unsigned int *llcount = nullptr;  // last-block counters (zero between launches): [0] log-likelihood total, [1] normalisation column sums
     double *colsum = nullptr;    // per-mode column sums [N x Rp]
     double *llpart = nullptr;    // per-tile log-likelihood partials
     cpapr::InnerState *inner = nullptr;  // [N]

@@ -132,9 +132,14 @@ cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, Inn
 // column sums (FP64), in a fixed order: block p sums rows p, p+P, ... per
 // column; the partials are then added in block order.
 // ---------------------------------------------------------------------------
+// With `counter` set, the block that finishes last (an atomic count, no
+// waiting) adds the partials in block order into colsum[0..Rp) and resets
+// the counter.
 template <typename T>
-__global__ void colsum_partial_kernel(const T *__restrict__ M, int64_t rows, int Rp, double *__restrict__ part) {
+__global__ void colsum_partial_kernel(const T *__restrict__ M, int64_t rows, int Rp, double *__restrict__ part,
+                                      unsigned int *counter = nullptr, double *__restrict__ colsum = nullptr) {
     __shared__ double sm[256];
+    __shared__ bool last;
     const int c = threadIdx.x % Rp;
     const int rl = threadIdx.x / Rp;
     const int nrl = blockDim.x / Rp;
@@ -149,6 +154,21 @@ __global__ void colsum_partial_kernel(const T *__restrict__ M, int64_t rows, int
         for (int k = 0; k < nrl; ++k) t += sm[k * Rp + threadIdx.x];
         part[(int64_t)blockIdx.x * Rp + threadIdx.x] = t;
     }
+    if (!counter) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int r = threadIdx.x; r < Rp; r += blockDim.x) {
+        double t = 0.0;
+        for (unsigned p = 0; p < gridDim.x; ++p) t += __ldcg(part + (int64_t)p * Rp + r);
+        colsum[r] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0;
 }
 
 static int colsum_parts(int64_t rows, int Rp) {
@@ -156,24 +176,25 @@ static int colsum_parts(int64_t rows, int Rp) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(kColParts, ceil_div(rows, nrl * 4)));
 }
 
-// lambda_c = sum of partials; A(i,c) = B(i,c) / lambda_c, or A kept when
-// lambda_c = 0 (an all-zero column).
+// A(i,c) = B(i,c) / lambda_c (lambda = the column sums of B, finished by
+// colsum_partial_kernel), or A kept when lambda_c = 0 (an all-zero column).
 template <typename T>
 __global__ void normalise_kernel(const T *__restrict__ B, T *__restrict__ A, int64_t rows, int Rp,
-                                 const double *__restrict__ part, int nparts, double *__restrict__ lambda) {
-    __shared__ double lam[256];
+                                 const double *__restrict__ lambda) {
+    // one reciprocal per column (no overflow: lambda >= 2^-1000, else a plain
+    // division); lambda = 0 marks an all-zero column, whose A stays
+    __shared__ double lam[256], inv[256];
     for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
-        double s = 0.0;
-        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * Rp + c];
-        lam[c] = s;
+        const double l = lambda[c];
+        lam[c] = l;
+        inv[c] = l >= 0x1p-1000 ? 1.0 / l : 0.0;
     }
     __syncthreads();
-    if (blockIdx.x == 0)
-        for (int c = threadIdx.x; c < Rp; c += blockDim.x) lambda[c] = lam[c];
     const int64_t n = rows * Rp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const double l = lam[e % Rp];
-        if (l > 0.0) A[e] = (T)((double)B[e] / l);
+        const int c = (int)(e & (Rp - 1));  // Rp is a power of two
+        const double l = lam[c];
+        if (l > 0.0) A[e] = (T)(inv[c] != 0.0 ? (double)B[e] * inv[c] : (double)B[e] / l);
     }
 }
 
@@ -185,14 +206,17 @@ cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
     if (n != ctx->pi_mode_built) ctx->pi_mode_built = -1;
     ProfScope ps(ctx, K_NORM);
     count_launch(ctx, 2);
+    // llcount[1]: the column-sum counter (llcount[0] belongs to the log-likelihood total)
     if (ctx->esize == 8) {
-        colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->B, rows, Rp, ctx->colpart);
+        colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->B, rows, Rp, ctx->colpart,
+                                                                      ctx->llcount + 1, ctx->lambda);
         normalise_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-            (const double *)ctx->B, (double *)ctx->A[n], rows, Rp, ctx->colpart, parts, ctx->lambda);
+            (const double *)ctx->B, (double *)ctx->A[n], rows, Rp, ctx->lambda);
     } else {
-        colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->B, rows, Rp, ctx->colpart);
+        colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->B, rows, Rp, ctx->colpart,
+                                                                     ctx->llcount + 1, ctx->lambda);
         normalise_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-            (const float *)ctx->B, (float *)ctx->A[n], rows, Rp, ctx->colpart, parts, ctx->lambda);
+            (const float *)ctx->B, (float *)ctx->A[n], rows, Rp, ctx->lambda);
     }
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
