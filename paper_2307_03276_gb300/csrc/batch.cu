@@ -10,6 +10,9 @@
 //                        check; per-tensor bookkeeping by the last block of
 //                        the tensor, loop condition by the last block overall
 //   batch_colsum/scale   lambda_t <- e^T B_t, A_t <- B_t Lambda_t^-1
+//   at the end           every tensor's log-likelihood: batch_scale_b_kernel,
+//                        batch_phi_kernel<..., OP_LL> over mode 0's tiles,
+//                        batch_ll_total_kernel
 // The inner loop is one CUDA graph with a conditional WHILE node whose body
 // is {phi, update}; it runs while any tensor still iterates.  Tensors
 // that converged are masked on the device (their kernels return at once).
@@ -23,12 +26,12 @@
 #include <mutex>
 #include <vector>
 
+#include "ll_total.cuh"
 #include "phi_kernels.cuh"
 
 namespace cpapr {
 
 cpapr_status configure_mode(cpapr_ctx *ctx, int n, int lanes, int tile, int reduction);
-cpapr_status loglik_enqueue(cpapr_ctx *ctx, double *host);
 
 namespace {
 
@@ -88,33 +91,35 @@ template <typename T> __host__ __device__ constexpr int batch_threads() { return
 // four-block case; every FP64 class fits three blocks (168 registers)
 template <typename T> __host__ __device__ constexpr int batch_min_blocks() { return sizeof(T) == 8 ? 3 : 4; }
 
-template <typename T, int NM1, int K, bool PI = false>
+template <typename T, int NM1, int K, int OP, bool PI = false>
 __device__ __forceinline__ bool run_class(const PhiArgs &a, int tile, unsigned char *smem, double *red, uint64_t *bar,
                                           uint32_t &phase) {
     constexpr int RPL = Classes<T>::rpl[K];
     constexpr int G = Classes<T>::g[K];
-    return phi_tile_body<T, NM1, RPL, G, OP_PHI, batch_threads<T>(), batch_unroll<T, RPL, G>(), PI>(a, tile, smem,
-                                                                                                   red, bar, phase);
+    return phi_tile_body<T, NM1, RPL, G, OP, batch_threads<T>(), batch_unroll<T, RPL, G>(), PI>(a, tile, smem, red,
+                                                                                               bar, phase);
 }
 
 // One item's tile with the tensor's rank class; FP64 tensors with
 // materialised Khatri-Rao rows (a.pi set) stream them.
-template <typename T, int NM1, bool PI>
+template <typename T, int NM1, int OP, bool PI>
 __device__ __forceinline__ bool run_item(const PhiArgs &a, int cfg, int tile, unsigned char *smem, double *red,
                                          uint64_t *bar, uint32_t &phase) {
     switch (cfg) {
-        case 0: return run_class<T, NM1, 0, PI>(a, tile, smem, red, bar, phase);
-        case 1: return run_class<T, NM1, 1, PI>(a, tile, smem, red, bar, phase);
-        case 2: return run_class<T, NM1, 2, PI>(a, tile, smem, red, bar, phase);
-        case 3: return run_class<T, NM1, 3, PI>(a, tile, smem, red, bar, phase);
+        case 0: return run_class<T, NM1, 0, OP, PI>(a, tile, smem, red, bar, phase);
+        case 1: return run_class<T, NM1, 1, OP, PI>(a, tile, smem, red, bar, phase);
+        case 2: return run_class<T, NM1, 2, OP, PI>(a, tile, smem, red, bar, phase);
+        case 3: return run_class<T, NM1, 3, OP, PI>(a, tile, smem, red, bar, phase);
         default:
             if constexpr (Classes<T>::n > 4)
-                return run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0), PI>(a, tile, smem, red, bar, phase);
+                return run_class<T, NM1, (Classes<T>::n > 4 ? 4 : 0), OP, PI>(a, tile, smem, red, bar, phase);
             return true;
     }
 }
 
-template <typename T, int NM1>
+// OP_PHI: Phi of every listed tile; OP_LL: the tile sums of x log m (the
+// descriptors then carry the scaled mode-0 B and no inner-loop state).
+template <typename T, int NM1, int OP = OP_PHI>
 __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) batch_phi_kernel(const BatchTensor *__restrict__ desc,
                                                                        const int2 *__restrict__ items, int nitems,
                                                                        BatchCtl *ctl) {
@@ -134,13 +139,13 @@ __global__ void __launch_bounds__(batch_threads<T>(), batch_min_blocks<T>()) bat
         if (it >= nitems) break;
         const int2 w = items[it];
         const PhiArgs a = desc[w.x].a;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8 && OP == OP_PHI) {
             if (a.pi) {
-                ok = run_item<T, NM1, true>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
+                ok = run_item<T, NM1, OP, true>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
                 continue;
             }
         }
-        ok = run_item<T, NM1, false>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
+        ok = run_item<T, NM1, OP, false>(a, desc[w.x].cfg, w.y, smem_raw, red, &bar, phase);
     }
     // the last block out resets the work counter for the next launch
     if (threadIdx.x == 0) {
@@ -354,6 +359,31 @@ __global__ void __launch_bounds__(256) batch_scale_kernel(const BatchTensor *__r
     }
 }
 
+// B_t = A_t^(0) Lambda_t for every tensor (the log-likelihood's scaled rows;
+// the same arithmetic as the single-tensor scale_b_kernel)
+template <typename T>
+__global__ void __launch_bounds__(256) batch_scale_b_kernel(const BatchTensor *__restrict__ desc,
+                                                            const int2 *__restrict__ chunks) {
+    const int2 w = chunks[blockIdx.x];
+    const BatchTensor &d = desc[w.x];
+    const int Rp = d.rp;
+    const int64_t r0 = (int64_t)w.y * kChunkRows;
+    const int64_t r1 = min(r0 + kChunkRows, d.rows);
+    const T *A = reinterpret_cast<const T *>(d.A);
+    T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
+    for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x)
+        B[e] = (T)((double)A[e] * d.lambda[e & (Rp - 1)]);
+}
+
+// Every tensor's log-likelihood total: item (t, b) is block b of tensor t's
+// total (the single-tensor launch's blocks, so the sums are the same).
+template <typename T>
+__global__ void __launch_bounds__(256) batch_ll_total_kernel(const LLTotalArgs *__restrict__ args,
+                                                             const int2 *__restrict__ items) {
+    const int2 w = items[blockIdx.x];
+    ll_total_body<T>(args[w.x], w.y);
+}
+
 __global__ void gather_states_kernel(InnerState *const *src, int n, InnerState *dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = *src[i];
@@ -383,6 +413,12 @@ struct Plan {
     InnerState **state_ptrs = nullptr;
     InnerState *states = nullptr;
     double *ll = nullptr;  // [count] final log-likelihoods
+    // the final log-likelihood: mode-0 descriptors without inner-loop state or
+    // materialised rows, each tensor's total arguments, and (tensor, block) items
+    BatchTensor *lldesc = nullptr;
+    LLTotalArgs *llargs = nullptr;
+    int2 *llitems = nullptr;
+    int nllitems = 0;
     std::vector<void *> owned;
     // what the plan was built for (it is reused while these match)
     std::vector<cpapr_ctx *> key;
@@ -408,6 +444,22 @@ cudaError_t launch_phi_batch(const ModePlan &mp, int nm1, int grid, BatchCtl *ct
         case 3: return go(batch_phi_kernel<T, 3>);
         case 4: return go(batch_phi_kernel<T, 4>);
         default: return go(batch_phi_kernel<T, 0>);
+    }
+}
+
+template <typename T>
+cudaError_t launch_ll_batch(const Plan &P, int nm1, int grid, cudaStream_t s) {
+    const ModePlan &m0 = P.modes[0];
+    auto go = [&](auto kern) {
+        if (m0.smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m0.smem);
+        kern<<<grid, batch_threads<T>(), m0.smem, s>>>(P.lldesc, m0.tiles, m0.ntiles, P.ctl);
+        return cudaGetLastError();
+    };
+    switch (nm1) {
+        case 2: return go(batch_phi_kernel<T, 2, OP_LL>);
+        case 3: return go(batch_phi_kernel<T, 3, OP_LL>);
+        case 4: return go(batch_phi_kernel<T, 4, OP_LL>);
+        default: return go(batch_phi_kernel<T, 0, OP_LL>);
     }
 }
 
@@ -582,6 +634,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         BT_CUDA(cudaMemcpy(P.state_ptrs, sp.data(), sp.size() * sizeof(InnerState *), cudaMemcpyHostToDevice));
     }
     size_t smem_max = 0;
+    std::vector<BatchTensor> desc0;
     for (int n = 0; n < N; ++n) {
         ModePlan &mp = P.modes[n];
         std::vector<BatchTensor> desc(count);
@@ -670,6 +723,25 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         if (!tiles.empty())
             BT_CUDA(cudaMemcpy(mp.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
         BT_CUDA(cudaMemcpy(mp.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        if (n == 0) desc0 = desc;
+    }
+    {
+        std::vector<LLTotalArgs> args(count);
+        std::vector<int2> items;
+        for (int i = 0; i < count; ++i) {
+            desc0[i].a.inner = nullptr;
+            desc0[i].a.pi = nullptr;
+            const int nll = ctxs[i]->nnz > 0 ? ctxs[i]->mode[0].ntiles : 0;
+            args[i] = ll_total_args(ctxs[i], ctxs[i]->llpart, nll, P.ll + i);
+            for (int b = 0; b < args[i].part0[N]; ++b) items.push_back(make_int2(i, b));
+        }
+        P.nllitems = (int)items.size();
+        BT_CUDA(dalloc((void **)&P.lldesc, (size_t)count * sizeof(BatchTensor)));
+        BT_CUDA(dalloc((void **)&P.llargs, (size_t)count * sizeof(LLTotalArgs)));
+        BT_CUDA(dalloc((void **)&P.llitems, items.size() * sizeof(int2)));
+        BT_CUDA(cudaMemcpy(P.lldesc, desc0.data(), (size_t)count * sizeof(BatchTensor), cudaMemcpyHostToDevice));
+        BT_CUDA(cudaMemcpy(P.llargs, args.data(), (size_t)count * sizeof(LLTotalArgs), cudaMemcpyHostToDevice));
+        BT_CUDA(cudaMemcpy(P.llitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     }
     if (smem_max > kMaxPhiSmem) {
         drop_cache_locked();
@@ -769,34 +841,25 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         drop_cache_locked();
         return st;
     }
-    // final log-likelihoods: every tensor on its own stream after the batch
-    // stream's work, into one device array that the batch stream copies back
-    // once all of them are done (one host wait for the whole batch)
+    // final log-likelihoods, three launches for the whole batch: B = A^(0)
+    // Lambda, the tile sums of x log m along mode 0 (rows formed in place),
+    // and every tensor's total; one copy back
     std::vector<double> ll(count, 0.0);
-    cudaEvent_t done_ev = nullptr;
-    CPAPR_CUDA(c0, cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(done_ev, s);
-    for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctxs[i]->stream, done_ev, 0);
-    if (e != cudaSuccess) {
-        cudaEventDestroy(done_ev);
-        return cuda_fail(c0, e, "batch log-likelihood ordering");
-    }
-    cpapr_status lst = CPAPR_OK;
-    for (int i = 0; i < count && lst == CPAPR_OK; ++i) {
-        lst = launch_loglik(ctxs[i], P.ll + i);
-        if (lst != CPAPR_OK) break;
-        // the batch stream waits for this tensor's sum (the event is re-recorded per tensor)
-        e = cudaEventRecord(done_ev, ctxs[i]->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done_ev, 0);
-        if (e != cudaSuccess) lst = cuda_fail(ctxs[i], e, "batch log-likelihood ordering");
-    }
-    if (lst == CPAPR_OK) {
-        e = cudaMemcpyAsync(ll.data(), P.ll, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, s);
+    {
+        const ModePlan &m0 = P.modes[0];
+        batch_scale_b_kernel<T><<<m0.nchunks, 256, 0, s>>>(m0.desc, m0.chunks);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && m0.ntiles > 0) e = launch_ll_batch<T>(P, N - 1, grid, s);
+        if (e == cudaSuccess) {
+            batch_ll_total_kernel<T><<<P.nllitems, 256, 0, s>>>(P.llargs, P.llitems);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ll.data(), P.ll, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) lst = cuda_fail(c0, e, "batch log-likelihood copy");
+        if (e != cudaSuccess) return cuda_fail(c0, e, "batch log-likelihood");
+        c0->launches += 3;
     }
-    cudaEventDestroy(done_ev);
-    if (lst != CPAPR_OK) return lst;
     for (int i = 0; i < count; ++i) {
         results[i].outer_iters = tr[i].outer;
         results[i].total_inner = tr[i].total;

@@ -63,6 +63,8 @@ def test_batch_fp64_equals_individual_solves_and_oracle(use_graph):
         for a, b in zip(fb, ref["factors"]):
             np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-14 * b.max())
         assert abs(r["loglik"] - ref["loglik"][-1]) <= 1e-11 * abs(ref["loglik"][-1])
+        # the batched log-likelihood launches against the single-tensor one on the same final model
+        assert abs(r["loglik"] - t.loglik()) <= 1e-13 * abs(r["loglik"])
         t.close()
     assert res[0]["converged"] and res[0]["outer_iters"] == 2
 
@@ -79,6 +81,7 @@ def test_batch_fp32_close_to_individual():
         ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=3, max_inner=5)
         np.testing.assert_allclose(lb, ref["lambda"], rtol=1e-4)
         assert abs(r["loglik"] - ref["loglik"][-1]) <= 1e-5 * abs(ref["loglik"][-1])
+        assert abs(r["loglik"] - t.loglik()) <= 1e-6 * abs(r["loglik"])
         t.close()
 
 
@@ -96,4 +99,29 @@ def test_batch_mixed_modes_falls_back():
         ref = oracle.mu_solve(T.dims, T.idx, T.vals, np.ones(4), synth.random_factors(T.dims, 4, 9), tol=1e-4,
                               max_outer=2, max_inner=3)
         np.testing.assert_allclose(t.get_model()[0], ref["lambda"], rtol=1e-10)
+        t.close()
+
+
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_batch_with_an_empty_tensor(precision):
+    """A tensor without nonzeros rides along in a batch: it gets no tiles, its
+    log-likelihood is the model total alone, and the other tensors' results
+    match their oracle solves."""
+    a = synth.random_tensor((40, 30, 20), 2_000, 8, 11)
+    ts = []
+    for dims, T in (((40, 30, 20), a), ((25, 15, 10), None)):
+        if T is None:
+            t = cpapr.Tensor(dims, np.zeros((3, 0), dtype=np.int64), np.zeros(0), 8, precision=precision)
+        else:
+            t = cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision)
+        t.set_model(np.ones(8), synth.random_factors(dims, 8, 12))
+        ts.append(t)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in ts], 1e-4, 2, 3)
+    ref = oracle.mu_solve(a.dims, a.idx, a.vals, np.ones(8), synth.random_factors(a.dims, 8, 12), tol=1e-4,
+                          max_outer=2, max_inner=3)
+    rt = 1e-11 if precision == cpapr.CPAPR_FP64 else 1e-5
+    assert abs(res[0]["loglik"] - ref["loglik"][-1]) <= rt * abs(ref["loglik"][-1])
+    for t, r in zip(ts, res):
+        ll = t.loglik()
+        assert np.isfinite(r["loglik"]) and abs(r["loglik"] - ll) <= 1e-12 * max(1.0, abs(ll))
         t.close()
