@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) batch_sb_kernel(const BatchTensor *__rest
     for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
         const double a = (double)A[e];
         const double s = (shift && a < d.kappa_tol && (double)P[e] > 1.0) ? d.kappa : 0.0;
-        B[e] = (T)((a + s) * d.lambda[e % Rp]);
+        B[e] = (T)((a + s) * d.lambda[e & (Rp - 1)]);  // Rp is a power of two
     }
 }
 
@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(256) batch_empty_kkt_kernel(const BatchTensor 
     const BatchTensor &d = desc[w.x];
     if (flags[2 * w.x]) return;
     const int Rp = d.rp;
+    const int lg = 31 - __clz(Rp);  // Rp is a power of two
     const int64_t q0 = (int64_t)w.y * kEmptyChunk;
     const int64_t q1 = min(q0 + kEmptyChunk, d.nempty * Rp);
     const T *B = reinterpret_cast<const T *>(d.a.B);
     T v = T(0);
     for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-        v = tmax(v, viol_t(B[(int64_t)d.erows[q / Rp] * Rp + q % Rp], T(0)));
+        v = tmax(v, viol_t(B[(int64_t)d.erows[q >> lg] * Rp + (q & (Rp - 1))], T(0)));
     publish_kkt<256>((double)v, d.a.inner, red);
 }
 
@@ -251,9 +252,12 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__
         const int Rp = d.rp;
         const int64_t r0 = (int64_t)w.y * kChunkRows;
         const int64_t r1 = min(r0 + kChunkRows, d.rows);
-        T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
-        const T *P = reinterpret_cast<const T *>(d.a.out);
-        for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) B[e] = B[e] * P[e];
+        // 16-byte vectors (a row is a whole number of them)
+        using V = typename Vec16<T>::type;
+        constexpr int W = Vec16<T>::n;
+        V *B = reinterpret_cast<V *>(const_cast<void *>(d.a.B));
+        const V *P = reinterpret_cast<const V *>(d.a.out);
+        for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x) B[e] = vmul(B[e], P[e]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

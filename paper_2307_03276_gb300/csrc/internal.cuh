@@ -223,6 +223,12 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
+// elementwise product of two 16-byte vectors
+__device__ __forceinline__ float4 vmul(float4 a, float4 b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
 __device__ __forceinline__ unsigned long long ordered_bits(double v) {
     // v >= 0: IEEE bit patterns of non-negative doubles order like the values
     return (unsigned long long)__double_as_longlong(v);

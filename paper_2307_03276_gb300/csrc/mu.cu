@@ -42,7 +42,7 @@ __global__ void sb_kernel(const T *__restrict__ A, const T *__restrict__ phi_pre
     }
     const int64_t n = rows * Rp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % Rp);
+        const int c = (int)(e & (Rp - 1));  // Rp is a power of two
         const double a = (double)A[e];
         const double s = (shift && a < kappa_tol && (double)phi_prev[e] > 1.0) ? kappa : 0.0;
         B[e] = (T)((a + s) * lambda[c]);
@@ -85,8 +85,13 @@ __global__ void update_kernel(T *__restrict__ B, const T *__restrict__ P, int64_
     const int l = s_l, done = s_done;
     const double viol = s_viol;
     if (!done && !(viol < tol)) {
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-            B[e] = B[e] * P[e];
+        // 16-byte vectors: n is a whole number of them (rows of Rp values)
+        using V = typename Vec16<T>::type;
+        V *Bv = reinterpret_cast<V *>(B);
+        const V *Pv = reinterpret_cast<const V *>(P);
+        const int64_t nv = n / Vec16<T>::n;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv; e += (int64_t)gridDim.x * blockDim.x)
+            Bv[e] = vmul(Bv[e], Pv[e]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -230,7 +235,7 @@ template <typename T>
 __global__ void scale_b_kernel(const T *__restrict__ A, const double *__restrict__ lambda, T *__restrict__ B,
                                int64_t n, int Rp) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        B[e] = (T)((double)A[e] * lambda[e % Rp]);
+        B[e] = (T)((double)A[e] * lambda[e & (Rp - 1)]);  // Rp is a power of two
 }
 
 cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB) {

@@ -961,19 +961,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) empty_kkt_kernel(const int32_t *__restrict__ erows, int64_t nempty, int Rp,
                                                          const T *__restrict__ B, InnerState *inner) {
     __shared__ double red[8];
+    const int lg = 31 - __clz(Rp);  // Rp is a power of two
     T v = T(0);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nempty * Rp;
          q += (int64_t)gridDim.x * blockDim.x)
-        v = tmax(v, viol_t(B[(int64_t)erows[q / Rp] * Rp + q % Rp], T(0)));
+        v = tmax(v, viol_t(B[(int64_t)erows[q >> lg] * Rp + (q & (Rp - 1))], T(0)));
     publish_kkt<256>((double)v, inner, red);
 }
 
 // Writes zeros into the rows without nonzeros.
 template <typename T>
 __global__ void zero_rows_kernel(const int32_t *__restrict__ erows, int64_t nempty, int Rp, T *__restrict__ out) {
+    const int lg = 31 - __clz(Rp);  // Rp is a power of two
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nempty * Rp;
          q += (int64_t)gridDim.x * blockDim.x)
-        out[(int64_t)erows[q / Rp] * Rp + q % Rp] = T(0);
+        out[(int64_t)erows[q >> lg] * Rp + (q & (Rp - 1))] = T(0);
 }
 
 // KKT violation over all rows (used after the atomic reduction).
