@@ -17,8 +17,10 @@ between steps; the factor matrices stay L2-resident by design.
 
 Reported beside it: the FP32 form of the same step, the roofline of the
 dominant kernel (the Phi tile kernel), an end-to-end number through the C
-ABI from pinned host buffers, MTTKRP kernel throughput, the clocks seen
-during the timed region and the FP64 oracle timed on the host's cores.
+ABI from pinned host buffers, MTTKRP kernel throughput, the batched solver,
+the time to KKT tolerance 1e-4 of the full solve (FP64 and FP32), the
+clocks seen during the timed region and the FP64 oracle timed on the host's
+cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   torchrun --nproc-per-node N bench.py --gpus N ...   (replicas: one per GPU)
@@ -292,6 +294,92 @@ def timed_solve(cp, torch, T, lam, fs, precision, steps, warmup, dist, use_cuda,
             "mttkrp": mt, "last": r}
 
 
+KKT_MAX_OUTER = 50
+
+
+def time_to_kkt(cp, torch, T, lam, fs, max_outer=KKT_MAX_OUTER):
+    """The full solve at KKT tolerance 1e-4 (Algorithm 1 until every mode
+    passes its check at the first inner iteration, or max_outer), FP64 and
+    FP32, each from the same initial model through the library's default
+    path (CUDA-graph inner loops); device time of the mu_solve call."""
+    stream = torch.cuda.current_stream()
+    out = {"workload": T.name, "kkt_tol": TOL, "max_outer": max_outer, "max_inner": MAX_INNER}
+    for name, prec in (("fp64", cp.CPAPR_FP64), ("fp32", cp.CPAPR_FP32)):
+        with cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=prec, stream=stream.cuda_stream) as t:
+            t.set_model(lam, fs)
+            t.mu_solve(TOL, 1, MAX_INNER)      # warm-up: graphs, plans, pools
+            t.set_model(lam, fs)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = t.mu_solve(TOL, max_outer, MAX_INNER)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        ll = r["loglik"]
+        # a model value that reached exactly 0 under a nonzero makes the
+        # log-likelihood -inf (reported as null: the JSON line stays strict)
+        out[name] = {"ms": ms, "outer_iters": r["outer_iters"], "total_inner": r["total_inner"],
+                     "converged": bool(r["converged"]), "kkt_viol": r["kkt_viol"],
+                     "loglik": ll if np.isfinite(ll) else None, "loglik_finite": bool(np.isfinite(ll)),
+                     "phi_nnz_per_s": r["total_inner"] * T.nnz / (ms / 1e3)}
+    out["fp32_speedup"] = out["fp64"]["ms"] / out["fp32"]["ms"]
+    l64, l32 = out["fp64"]["loglik"], out["fp32"]["loglik"]
+    out["loglik_rel_diff"] = abs(l32 - l64) / abs(l64) if (l64 is not None and l32 is not None) else None
+    return out
+
+
+def batch_time_to_kkt(cp, torch, max_outer=KKT_MAX_OUTER, count=64):
+    """The 64-tensor batch solved to KKT tolerance 1e-4 (or max_outer) by the
+    batched solver and by one mu_solve per tensor, FP64 and FP32."""
+    from paper_2307_03276_gb300 import synth
+    tensors = [synth.generate(sp) for sp in synth.batch_specs(count=count)]
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"c4_batch{count}_3way", "kkt_tol": TOL, "max_outer": max_outer}
+    for pname, prec in (("fp64", cp.CPAPR_FP64), ("fp32", cp.CPAPR_FP32)):
+        for mode in ("batched", "per_tensor"):
+            ts = [cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=prec, stream=stream.cuda_stream) for T in tensors]
+            init = [(np.ones(T.rank), synth.random_factors(T.dims, T.rank, T.seed + 3)) for T in tensors]
+
+            def solve(mo):
+                for t, (lam, fs) in zip(ts, init):
+                    t.set_model(lam, fs)
+                if mode == "batched":
+                    return cp.cpapr_batch_mu_solve([t.ctx for t in ts], TOL, mo, MAX_INNER)
+                return [t.mu_solve(TOL, mo, MAX_INNER) for t in ts]
+
+            solve(1)  # warm-up
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = solve(max_outer)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            for t in ts:
+                t.close()
+            out[f"{pname}_{mode}"] = {"ms": ms, "converged": sum(bool(r["converged"]) for r in res),
+                                      "outer_iters_max": max(r["outer_iters"] for r in res),
+                                      "total_inner": sum(r["total_inner"] for r in res),
+                                      "phi_nnz_per_s": sum(r["total_inner"] * T.nnz for r, T in zip(res, tensors))
+                                      / (ms / 1e3)}
+    return out
+
+
+def run_time_to_kkt(args):
+    import torch
+    from paper_2307_03276_gb300 import build, cpapr as cp
+    torch.cuda.set_device(0)
+    build.build()
+    if args.workload == "c4":
+        print(json.dumps({"probe": "time_to_kkt", **batch_time_to_kkt(cp, torch, args.max_outer)}), flush=True)
+        return
+    T, lam, fs = make_workload(args.workload)
+    print(json.dumps({"probe": "time_to_kkt", **time_to_kkt(cp, torch, T, lam, fs, args.max_outer)}), flush=True)
+
+
 def batched_run(cp, torch, precision, steps, warmup, count=64):
     """64 uneven 3-way tensors (dims log-uniform up to 20000 x 20000 x 500, nnz
     log-uniform 1e3..1e6, R in {8, 16, 32}): one outer iteration per step for
@@ -512,6 +600,8 @@ def run_ours(args):
                                b["batched"]["ms_per_step"] * args.steps / 1e3, use_cuda)
             b["batched"]["value"] = ub / sb
             out["variants"]["batched_" + pname] = b
+        if world == 1:
+            out["variants"]["time_to_kkt"] = time_to_kkt(cp, torch, T, lam, fs)
     out["kernels"] = kern
     if not args.no_e2e:
         e2e = e2e_run(cp, torch, T, lam, fs, prim, max(2, args.steps // 2), 1)
@@ -724,7 +814,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c4 (the 64-tensor batch) applies to --time-to-kkt only")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "both"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -736,12 +827,20 @@ def main(argv=None):
     ap.add_argument("--ranks", default="8,16,32,64")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only run Phi^(n) for every mode --steps times (profiling target)")
+    ap.add_argument("--time-to-kkt", action="store_true",
+                    help="full solve at KKT tolerance 1e-4 (FP64 and FP32) on --workload")
+    ap.add_argument("--max-outer", type=int, default=KKT_MAX_OUTER)
     ap.add_argument("--ppa", action="store_true",
                     help="pressure-point probes: factor-row reuse and atomic vs segmented reduction")
     args = ap.parse_args(argv)
     if args.ppa:
         run_ppa(args)
         return
+    if args.time_to_kkt:
+        run_time_to_kkt(args)
+        return
+    if args.workload == "c4":
+        raise SystemExit("--workload c4 (the 64-tensor batch) applies to --time-to-kkt only")
     if args.r_sweep:
         if args.workload == "c2":
             args.workload = "c5"

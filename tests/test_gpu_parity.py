@@ -235,6 +235,26 @@ def test_mu_solve_fp64_4way_two_outer():
         np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
 
 
+def test_mu_solve_fp64_long_horizon():
+    """Twelve outer iterations of ten inner iterations on the 200,000-nonzero
+    3-way Zipf tensor: the log-likelihood after every outer iteration, the
+    final KKT violation and the model follow the oracle's trajectory (no
+    drift: the two agree to a few ulps after 360 Phi evaluations)."""
+    T = case("c2s")
+    lam, fs = model_for(T, 23)
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=12, max_inner=10)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        t.set_model(lam, fs)
+        res = t.mu_solve(tol=1e-4, max_outer=12, max_inner=10, trace=True, ll_trace=True)
+        lam_g, fs_g = t.get_model()
+    assert res["outer_iters"] == ref["outer_iters"] and np.array_equal(res["inner"], ref["inner"])
+    assert max_rel(res["loglik_trace"], ref["loglik"]) <= 1e-12
+    assert abs(res["kkt_viol"] - ref["kkt"][-1]) <= 1e-9 * ref["kkt"][-1]
+    assert max_rel(lam_g, ref["lambda"]) <= 1e-10
+    for A, Ar in zip(fs_g, ref["factors"]):
+        np.testing.assert_allclose(A, Ar, rtol=1e-8, atol=1e-14 * Ar.max())
+
+
 def test_mu_solve_fp32_close_to_oracle():
     T = case("c1")
     lam, fs = model_for(T, 23)
