@@ -618,13 +618,30 @@ def run_ours(args):
 
 
 def run_kernel_only(args):
-    """Phi^(n) for every mode, `steps` rounds: a small target for ncu captures."""
+    """Phi^(n) for every mode, `steps` rounds: a small target for ncu captures.
+    With --workload c4: `steps` batched outer iterations of the 64-tensor
+    batch with plain stream launches (no graphs, so every kernel is visible
+    to a launch list)."""
     import torch
     from paper_2307_03276_gb300 import build, cpapr as cp
     torch.cuda.set_device(0)
     build.build()
-    T, lam, fs = make_workload(args.workload)
     prec = cp.CPAPR_FP64 if args.precision == "fp64" else cp.CPAPR_FP32
+    if args.workload == "c4":
+        from paper_2307_03276_gb300 import synth
+        tensors = [synth.generate(sp) for sp in synth.batch_specs(count=64)]
+        ts = [cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=prec, use_graph=0) for T in tensors]
+        for T, t in zip(tensors, ts):
+            t.set_model(np.ones(T.rank), synth.random_factors(T.dims, T.rank, T.seed + 3))
+        inner = 0
+        for _ in range(args.steps):
+            inner += sum(r["total_inner"] for r in cp.cpapr_batch_mu_solve([t.ctx for t in ts], TOL, 1, MAX_INNER))
+        for t in ts:
+            t.close()
+        print(json.dumps({"kernel": "batch", "precision": args.precision, "workload": "c4_batch64_3way",
+                          "outer_iterations": args.steps, "inner_iterations": inner}))
+        return
+    T, lam, fs = make_workload(args.workload)
     with cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=prec, profile=1, use_graph=0) as t:
         t.set_model(lam, fs)
         for _ in range(args.steps):
@@ -815,7 +832,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
-                    help="c4 (the 64-tensor batch) applies to --time-to-kkt only")
+                    help="c4 (the 64-tensor batch) applies to --time-to-kkt and --kernel-only only")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "both"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -839,8 +856,8 @@ def main(argv=None):
     if args.time_to_kkt:
         run_time_to_kkt(args)
         return
-    if args.workload == "c4":
-        raise SystemExit("--workload c4 (the 64-tensor batch) applies to --time-to-kkt only")
+    if args.workload == "c4" and not args.kernel_only:
+        raise SystemExit("--workload c4 (the 64-tensor batch) applies to --time-to-kkt and --kernel-only only")
     if args.r_sweep:
         if args.workload == "c2":
             args.workload = "c5"
