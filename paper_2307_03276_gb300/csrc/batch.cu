@@ -319,11 +319,9 @@ __global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchTensor *__
         for (int k = 0; k < nrl; ++k) t += sm[k * Rp + threadIdx.x];
         d.colpart[(int64_t)w.y * Rp + threadIdx.x] = t;
     }
+    __threadfence();  // every writer's partial is visible device-wide before the count
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&chunk_count[w.x], 1u) == (unsigned)d.nchunks - 1;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&chunk_count[w.x], 1u) == (unsigned)d.nchunks - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();

@@ -161,11 +161,9 @@ __global__ void colsum_partial_kernel(const T *__restrict__ M, int64_t rows, int
         part[(int64_t)blockIdx.x * Rp + threadIdx.x] = t;
     }
     if (!counter) return;
+    __threadfence();  // every writer's partial is visible device-wide before the count
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
