@@ -291,12 +291,19 @@ cpapr_status configure_l2_window(cpapr_ctx *ctx) {
     CPAPR_CUDA(ctx, cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
     if (max_persist <= 0 || max_window <= 0 || ctx->factor_bytes == 0) return CPAPR_OK;
     const size_t window = std::min(ctx->factor_bytes, (size_t)max_window);
+    // a device or mode that refuses the set-aside leaves the option without effect
     size_t setaside = 0;
-    CPAPR_CUDA(ctx, cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize));
+    if (cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        cudaGetLastError();
+        return CPAPR_OK;
+    }
     const size_t want = std::min(window, (size_t)max_persist);
     if (setaside < want) {
-        CPAPR_CUDA(ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
-        CPAPR_CUDA(ctx, cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize));
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess ||
+            cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+            cudaGetLastError();
+            return CPAPR_OK;
+        }
     }
     if (setaside == 0) return CPAPR_OK;
     ctx->l2win.base_ptr = ctx->factor_block;
