@@ -101,7 +101,8 @@ enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
  *             persisting-L2 set-aside raised to cover it (up to the device
  *             maximum; never lowered; persisting lines are returned to normal
  *             when the context is destroyed).  0 = off (default).  Ignored
- *             on devices without persisting L2.
+ *             on devices without persisting L2 or that refuse the set-aside
+ *             (cpapr_get_info then reports l2_window_bytes = 0).
  */
 typedef struct {
     int32_t precision;
