@@ -579,3 +579,38 @@ def test_l2_persist_window_changes_no_result(precision, pi_mode):
     assert np.array_equal(a[4][0], b[4][0])
     for x, y in zip(a[4][1], b[4][1]):
         assert np.array_equal(x, y)
+
+
+def test_torch_device_buffers_and_stream():
+    """The boundary tells host from device buffers by their attributes: a
+    context on torch's current stream takes its model from CUDA tensors and
+    writes Phi, MTTKRP and the model into CUDA tensors, with the same values
+    as through host arrays."""
+    import ctypes
+    import torch
+    T = case("c1")
+    lam, fs = model_for(T, 24)
+    stream = torch.cuda.current_stream()
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as h:
+        h.set_model(lam, fs)
+        want_phi = [h.phi(n) for n in range(T.nmodes)]
+        want_mtt = [h.mttkrp(n) for n in range(T.nmodes)]
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, stream=stream.cuda_stream) as t:
+        t.set_model(torch.from_numpy(lam).cuda(), [torch.from_numpy(np.ascontiguousarray(A)).cuda() for A in fs])
+        for n in range(T.nmodes):
+            out = torch.full((T.dims[n], T.rank), float("nan"), dtype=torch.float64, device="cuda")
+            t.phi(n, out=out)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), want_phi[n])
+            out.fill_(float("nan"))
+            t.mttkrp(n, out=out)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), want_mtt[n])
+        lam_d = torch.zeros(T.rank, dtype=torch.float64, device="cuda")
+        fs_d = [torch.zeros((d, T.rank), dtype=torch.float64, device="cuda") for d in T.dims]
+        arr = (ctypes.c_void_p * T.nmodes)(*[A.data_ptr() for A in fs_d])
+        assert cpapr.load().cpapr_get_model(t.ctx, ctypes.c_void_p(lam_d.data_ptr()), arr) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(lam_d.cpu().numpy(), t.get_model()[0])
+        for A, Ar in zip(fs_d, t.get_model()[1]):
+            assert np.array_equal(A.cpu().numpy(), Ar)
