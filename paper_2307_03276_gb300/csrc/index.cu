@@ -8,7 +8,8 @@
 // streams them contiguously instead of reading through a permutation array
 // (the paper notes that indirect access through the permutation is slow).
 //
-// Steps (all on the device):
+// Steps (all on the device; the copies of step 1 run on a second stream and
+// overlap the sorts of the modes already copied):
 //   1. copy the int64 COO in, check 0 <= i_m < I_m and x finite and >= 0,
 //      narrow coordinates to int32;
 //   2. per mode n: stable LSD radix sort of (i_n, position) with 8-bit digits
@@ -294,19 +295,44 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
     ctx->nnz_pad = ceil_div(std::max<int64_t>(nnz, 1), 256) * 256 + 256;
     const int64_t np = ctx->nnz_pad;
 
+    // The input crosses to the device on a second stream, one array at a
+    // time, while the main stream narrows and sorts the modes that have
+    // arrived (mode n's sort needs only its own coordinates); the gathers,
+    // which need every array, follow.  Invalid input is flagged by the
+    // device (and clamped, so every later index stays in bounds) and
+    // reported once everything has run.
     int32_t *idx32[kMaxModes] = {};
+    int64_t *stage[kMaxModes] = {};
+    uint32_t *perm[kMaxModes] = {};
+    uint32_t *flags[kMaxModes] = {};
     double *vals = nullptr;
-    int64_t *stage = nullptr;
-    uint32_t *keys = nullptr, *perm = nullptr, *tk = nullptr, *tv = nullptr;
+    uint32_t *keys = nullptr, *tk = nullptr, *tv = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kMaxModes + 2] = {};
     auto cleanup = [&]() {
-        for (int m = 0; m < N; ++m)
+        // the copies finish before their buffers go back to the pool
+        if (cs) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, cs);
+                cudaStreamWaitEvent(s, e, 0);
+                cudaEventDestroy(e);
+            }
+        }
+        for (int m = 0; m < N; ++m) {
             if (idx32[m]) cudaFreeAsync(idx32[m], s);
+            if (stage[m]) cudaFreeAsync(stage[m], s);
+            if (perm[m]) cudaFreeAsync(perm[m], s);
+            if (flags[m]) cudaFreeAsync(flags[m], s);
+        }
         if (vals) cudaFreeAsync(vals, s);
-        if (stage) cudaFreeAsync(stage, s);
         if (keys) cudaFreeAsync(keys, s);
-        if (perm) cudaFreeAsync(perm, s);
         if (tk) cudaFreeAsync(tk, s);
         if (tv) cudaFreeAsync(tv, s);
+        cudaStreamSynchronize(s);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
     };
 #define BL_CUDA(call)                                      \
     do {                                                   \
@@ -327,24 +353,101 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
 
     const int64_t nb = std::max<int64_t>(nnz, 1);
     BL_CUDA(cudaMemsetAsync(ctx->errflag, 0, 16, s));
-    BL_CUDA(lib_malloc((void **)&stage, nb * 8, s));
-    BL_CUDA(lib_malloc((void **)&vals, nb * 8, s));
-    for (int m = 0; m < N; ++m) {
-        BL_CUDA(lib_malloc((void **)&idx32[m], nb * 4, s));
-        if (nnz > 0) {
-            BL_CUDA(cudaMemcpyAsync(stage, idx_in[m], nnz * 8, cudaMemcpyDefault, s));
-            narrow_check_kernel<<<grid_for(nnz), 256, 0, s>>>(stage, nnz, ctx->dims[m], idx32[m], ctx->errflag);
-            count_launch(ctx);
-            BL_CUDA(cudaGetLastError());
+    // the layouts themselves (owned by the context); only the padding past
+    // nnz needs a value before the streams are written
+    for (int n = 0; n < N; ++n) {
+        ModeLayout &L = ctx->mode[n];
+        L.In = (int32_t)ctx->dims[n];
+        void *p = nullptr;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)(L.In + 1) * 4));
+        L.seg = (int32_t *)p;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
+        L.rid = (int32_t *)p;
+        BL_CUDA(cudaMemsetAsync(L.rid + nnz, 0xff, (size_t)(np - nnz) * 4, s));  // -1: no row past the last nonzero
+        for (int k = 0; k < N - 1; ++k) {
+            BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
+            L.idx[k] = (int32_t *)p;
+            BL_CUDA(cudaMemsetAsync(L.idx[k] + nnz, 0, (size_t)(np - nnz) * 4, s));
         }
+        BL_TRY(dev_alloc(ctx, &p, (size_t)np * ctx->esize));
+        L.val = p;
+        BL_CUDA(cudaMemsetAsync((char *)p + (size_t)nnz * ctx->esize, 0, (size_t)(np - nnz) * ctx->esize, s));
+        if (nnz == 0) BL_CUDA(cudaMemsetAsync(L.seg, 0, (size_t)(L.In + 1) * 4, s));
     }
     if (nnz > 0) {
-        BL_CUDA(cudaMemcpyAsync(vals, vals_in, nnz * 8, cudaMemcpyDefault, s));
+        for (int m = 0; m < N; ++m) {
+            BL_CUDA(lib_malloc((void **)&stage[m], nb * 8, s));
+            BL_CUDA(lib_malloc((void **)&idx32[m], nb * 4, s));
+            BL_CUDA(lib_malloc((void **)&perm[m], nb * 4, s));
+        }
+        BL_CUDA(lib_malloc((void **)&vals, nb * 8, s));
+        BL_CUDA(lib_malloc((void **)&keys, nb * 4, s));
+        BL_CUDA(lib_malloc((void **)&tk, nb * 4, s));
+        BL_CUDA(lib_malloc((void **)&tv, nb * 4, s));
+        BL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        for (int k = 0; k <= N + 1; ++k) BL_CUDA(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+        // the copy stream starts after the allocations above
+        BL_CUDA(cudaEventRecord(ev[N + 1], s));
+        BL_CUDA(cudaStreamWaitEvent(cs, ev[N + 1], 0));
+        for (int n = 0; n < N; ++n) {
+            BL_CUDA(cudaMemcpyAsync(stage[n], idx_in[n], nnz * 8, cudaMemcpyDefault, cs));
+            BL_CUDA(cudaEventRecord(ev[n], cs));
+            BL_CUDA(cudaStreamWaitEvent(s, ev[n], 0));
+            narrow_check_kernel<<<grid_for(nnz), 256, 0, s>>>(stage[n], nnz, ctx->dims[n], idx32[n], ctx->errflag);
+            BL_CUDA(cudaGetLastError());
+            BL_CUDA(cudaFreeAsync(stage[n], s));
+            stage[n] = nullptr;
+            // sort mode n by its row: sorted row ids (rid), row offsets (seg), the permutation
+            ModeLayout &L = ctx->mode[n];
+            BL_CUDA(cudaMemcpyAsync(keys, idx32[n], nnz * 4, cudaMemcpyDeviceToDevice, s));
+            iota_kernel<<<grid_for(nnz), 256, 0, s>>>(perm[n], nnz);
+            BL_CUDA(cudaGetLastError());
+            int bits = 0;
+            while (bits < 31 && ((int64_t)1 << bits) < (int64_t)L.In) ++bits;
+            BL_TRY(radix_sort(ctx, keys, perm[n], tk, tv, nnz, bits));
+            seg_kernel<<<grid_for(nnz), 256, 0, s>>>(keys, nnz, L.In, L.seg);
+            BL_CUDA(cudaGetLastError());
+            BL_CUDA(cudaMemcpyAsync(L.rid, keys, nnz * 4, cudaMemcpyDeviceToDevice, s));
+            count_launch(ctx, 3);  // narrow, iota, seg
+        }
+        BL_CUDA(cudaMemcpyAsync(vals, vals_in, nnz * 8, cudaMemcpyDefault, cs));
+        BL_CUDA(cudaEventRecord(ev[N], cs));
+        BL_CUDA(cudaStreamWaitEvent(s, ev[N], 0));
         check_values_kernel<<<grid_for(nnz), 256, 0, s>>>(vals, nnz, ctx->errflag);
-        count_launch(ctx);
         BL_CUDA(cudaGetLastError());
+        count_launch(ctx);
+        // every mode's other coordinates and values in its sorted order
+        for (int n = 0; n < N; ++n) {
+            ModeLayout &L = ctx->mode[n];
+            int k = 0;
+            for (int m = 0; m < N; ++m) {
+                if (m == n) continue;
+                gather_i32_kernel<<<grid_for(nnz), 256, 0, s>>>(idx32[m], perm[n], nnz, L.idx[k]);
+                BL_CUDA(cudaGetLastError());
+                ++k;
+            }
+            if (ctx->esize == 8)
+                gather_val_kernel<double><<<grid_for(nnz), 256, 0, s>>>(vals, perm[n], nnz, (double *)L.val);
+            else
+                gather_val_kernel<float><<<grid_for(nnz), 256, 0, s>>>(vals, perm[n], nnz, (float *)L.val);
+            BL_CUDA(cudaGetLastError());
+            count_launch(ctx, N);
+        }
     }
+    // per mode: the rows without nonzeros (their Phi row is zero); the counts
+    // of all modes come back in one synchronisation, with the input flags
+    for (int n = 0; n < N; ++n) {
+        ModeLayout &L = ctx->mode[n];
+        BL_CUDA(lib_malloc((void **)&flags[n], (size_t)(L.In + 1) * 4, s));
+        empty_flags_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flags[n]);
+        BL_CUDA(cudaGetLastError());
+        BL_TRY(exclusive_scan_u32(ctx, flags[n], L.In, flags[n] + L.In));
+        count_launch(ctx);
+    }
+    uint32_t totals[kMaxModes] = {};
     int32_t hflag[4] = {0, 0, 0, 0};
+    for (int n = 0; n < N; ++n)
+        BL_CUDA(cudaMemcpyAsync(&totals[n], flags[n] + ctx->mode[n].In, 4, cudaMemcpyDeviceToHost, s));
     BL_CUDA(cudaMemcpyAsync(hflag, ctx->errflag, 16, cudaMemcpyDeviceToHost, s));
     BL_CUDA(cudaStreamSynchronize(s));
     if (hflag[0]) {
@@ -355,85 +458,15 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         cleanup();
         return fail(ctx, CPAPR_E_VALUE, "a tensor value is negative, NaN or infinite");
     }
-    cudaFreeAsync(stage, s);
-    stage = nullptr;
-
-    BL_CUDA(lib_malloc((void **)&keys, nb * 4, s));
-    BL_CUDA(lib_malloc((void **)&perm, nb * 4, s));
-    BL_CUDA(lib_malloc((void **)&tk, nb * 4, s));
-    BL_CUDA(lib_malloc((void **)&tv, nb * 4, s));
-
     for (int n = 0; n < N; ++n) {
         ModeLayout &L = ctx->mode[n];
-        L.In = (int32_t)ctx->dims[n];
-        void *p = nullptr;
-        BL_TRY(dev_alloc(ctx, &p, (size_t)(L.In + 1) * 4));
-        L.seg = (int32_t *)p;
-        BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
-        L.rid = (int32_t *)p;
-        BL_CUDA(cudaMemsetAsync(p, 0xff, (size_t)np * 4, s));  // -1: no row past the last nonzero
-        int k = 0;
-        for (int m = 0; m < N; ++m) {
-            if (m == n) continue;
-            BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
-            L.idx[k] = (int32_t *)p;
-            BL_CUDA(cudaMemsetAsync(p, 0, (size_t)np * 4, s));
-            ++k;
-        }
-        BL_TRY(dev_alloc(ctx, &p, (size_t)np * ctx->esize));
-        L.val = p;
-        BL_CUDA(cudaMemsetAsync(p, 0, (size_t)np * ctx->esize, s));
-        if (nnz == 0) {
-            BL_CUDA(cudaMemsetAsync(L.seg, 0, (size_t)(L.In + 1) * 4, s));
-            continue;
-        }
-        BL_CUDA(cudaMemcpyAsync(keys, idx32[n], nnz * 4, cudaMemcpyDeviceToDevice, s));
-        iota_kernel<<<grid_for(nnz), 256, 0, s>>>(perm, nnz);
-        count_launch(ctx, 2 + ctx->N);  // iota, seg, N-1 index gathers, value gather
-        BL_CUDA(cudaGetLastError());
-        int bits = 0;
-        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)L.In) ++bits;
-        BL_TRY(radix_sort(ctx, keys, perm, tk, tv, nnz, bits));
-        seg_kernel<<<grid_for(nnz), 256, 0, s>>>(keys, nnz, L.In, L.seg);
-        BL_CUDA(cudaGetLastError());
-        BL_CUDA(cudaMemcpyAsync(L.rid, keys, nnz * 4, cudaMemcpyDeviceToDevice, s));
-        k = 0;
-        for (int m = 0; m < N; ++m) {
-            if (m == n) continue;
-            gather_i32_kernel<<<grid_for(nnz), 256, 0, s>>>(idx32[m], perm, nnz, L.idx[k]);
-            BL_CUDA(cudaGetLastError());
-            ++k;
-        }
-        if (ctx->esize == 8)
-            gather_val_kernel<double><<<grid_for(nnz), 256, 0, s>>>(vals, perm, nnz, (double *)L.val);
-        else
-            gather_val_kernel<float><<<grid_for(nnz), 256, 0, s>>>(vals, perm, nnz, (float *)L.val);
-        BL_CUDA(cudaGetLastError());
-    }
-    // per mode: the rows without nonzeros (their Phi row is zero)
-    for (int n = 0; n < N; ++n) {
-        ModeLayout &L = ctx->mode[n];
-        uint32_t *flag = nullptr;
-        BL_CUDA(lib_malloc((void **)&flag, (size_t)(L.In + 1) * 4, s));
-        empty_flags_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flag);
-        BL_CUDA(cudaGetLastError());
-        cpapr_status st = exclusive_scan_u32(ctx, flag, L.In, flag + L.In);
-        if (st != CPAPR_OK) {
-            cudaFreeAsync(flag, s);
-            cleanup();
-            return st;
-        }
-        uint32_t total = 0;
-        BL_CUDA(cudaMemcpyAsync(&total, flag + L.In, 4, cudaMemcpyDeviceToHost, s));
-        BL_CUDA(cudaStreamSynchronize(s));
-        L.nempty = (int32_t)total;
+        L.nempty = (int32_t)totals[n];
         void *p = nullptr;
         BL_TRY(dev_alloc(ctx, &p, (size_t)std::max<int32_t>(L.nempty, 1) * 4));
         L.erows = (int32_t *)p;
-        empty_write_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flag, L.erows);
+        empty_write_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flags[n], L.erows);
         BL_CUDA(cudaGetLastError());
-        count_launch(ctx, 2);
-        BL_CUDA(cudaFreeAsync(flag, s));
+        count_launch(ctx);
     }
     cleanup();
     BL_CUDA(cudaStreamSynchronize(s));
