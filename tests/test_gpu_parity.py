@@ -614,3 +614,34 @@ def test_torch_device_buffers_and_stream():
         assert np.array_equal(lam_d.cpu().numpy(), t.get_model()[0])
         for A, Ar in zip(fs_d, t.get_model()[1]):
             assert np.array_equal(A.cpu().numpy(), Ar)
+
+
+@pytest.mark.parametrize("where", ["pinned", "cuda"])
+def test_create_from_pinned_and_device_inputs(where):
+    """The index build reads device inputs in place (no staging copy) and
+    host ones, pinned or pageable, through a copy: the layouts, and so every
+    Phi, are the same; invalid coordinates are reported as E_RANGE on every
+    route."""
+    import torch
+    T = case("c2s")
+    lam, fs = model_for(T, 25)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as h:
+        h.set_model(lam, fs)
+        want = [h.phi(n) for n in range(T.nmodes)]
+    idx_t = torch.from_numpy(T.idx)
+    val_t = torch.from_numpy(T.vals)
+    if where == "pinned":
+        idx_t, val_t = idx_t.pin_memory(), val_t.pin_memory()
+    else:
+        idx_t, val_t = idx_t.cuda(), val_t.cuda()
+    with cpapr.Tensor(T.dims, [idx_t[m] for m in range(T.nmodes)], val_t, T.rank) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            assert np.array_equal(t.phi(n), want[n])
+    bad = idx_t.clone()
+    bad[1, 7] = T.dims[1]
+    if where == "pinned":
+        bad = bad.pin_memory()
+    with pytest.raises(cpapr.CpaprError) as e:
+        cpapr.Tensor(T.dims, [bad[m] for m in range(T.nmodes)], val_t, T.rank)
+    assert e.value.status == 2
