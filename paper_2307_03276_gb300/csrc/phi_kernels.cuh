@@ -914,10 +914,11 @@ __device__ __forceinline__ void pi_build_range(const PhiArgs &a, T *__restrict__
     constexpr int VN = Vec16<T>::n;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
     const int nm1 = NM1 > 0 ? NM1 : a.nm1;
-    const int vpr = a.Rp / VN;  // vectors per row
+    const int vpr = a.Rp / VN;  // vectors per row, a power of two (Rp is one)
+    const int lg = 31 - __clz(vpr);
     for (int64_t e = e0; e < e1; e += step) {
-        const int64_t p = e / vpr;
-        const int c = (int)(e - p * vpr) * VN;
+        const int64_t p = e >> lg;
+        const int c = (int)(e & (vpr - 1)) * VN;
         V x = __ldg(reinterpret_cast<const V *>(reinterpret_cast<const T *>(a.A[0]) +
                                                 (int64_t)__ldg(a.idx[0] + p) * a.Rp + c));
 #pragma unroll
