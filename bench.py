@@ -480,6 +480,10 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     roof["launches"] = launches
     roof["hbm"] = hbm
     roof["l2_gather"] = l2g
+    # the paper's word count Q = nnz(5R+2) 8-byte words per Phi (Eq. "Q"), which
+    # counts every factor access whether it hits a cache or not: context only
+    qb = sum(inner_per_mode[n] * nnz * (5 * R + 2) * 8.0 for n in range(N))
+    roof["paper_model"] = {"achieved": qb / sec / 1e9, "unit": "GB/s", "words_per_nonzero": 5 * R + 2}
     roof["flops_tflops"] = fl / sec / 1e12
     return roof
 
