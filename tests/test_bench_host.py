@@ -77,3 +77,33 @@ def test_window_mode_distribution():
     counts = np.bincount(T.idx[1], minlength=8)
     assert counts.min() > 0.8 * T.nnz / 8  # near-uniform over the window
     assert len({tuple(c) for c in T.idx.T}) == T.nnz
+
+
+def test_roofline_line_is_strict_json():
+    """The roofline object of a measured FP64 step: the FLOP model of the Pi
+    form that ran, the measured traffic for a captured configuration, the
+    paper's word count as context, and nothing a strict JSON parser rejects."""
+    import json
+
+    class CP:
+        CPAPR_FP64, CPAPR_FP32, CPAPR_PI_MATERIALISED, K_PHI = 0, 1, 2, 0
+
+    class Info:
+        rank_lanes = (4, 4, 4)
+        tile_nnz = (1024, 1024, 1024)
+
+    class T:
+        nmodes, nnz, rank = 3, 10_000_000, 32
+        dims = (100_000, 100_000, 1_000)
+        name = "c2_3way_1e5x1e5x1e3_1e7_r32"
+
+    inner = np.array([10, 10, 10])
+    r = bench.roofline_for(T, inner, {0: (30, 43.6)}, 0, {"hbm_gbs": 6682.5, "source": "measured"}, CP,
+                           [2, 2, 2], Info())
+    json.dumps(r, allow_nan=False)
+    assert r["bound"] == "alu" and r["flop_model"] == "4R+2 per nonzero"
+    flops = 30 * 1e7 * (4 * 32 + 2)
+    assert abs(r["achieved"] - flops / 43.6e-3 / 1e12) < 1e-9
+    assert r["traffic"] is not None and 2.7e9 < r["traffic"] < 2.9e9
+    assert r["paper_model"]["words_per_nonzero"] == 162
+    assert abs(r["paper_model"]["achieved"] - 30 * 1e7 * 162 * 8 / 43.6e-3 / 1e9) < 1e-6
