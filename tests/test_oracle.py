@@ -216,3 +216,32 @@ def test_oracle_rejects_out_of_range(oracle):
     idx[1, 3] = 3
     with pytest.raises(ValueError):
         oracle.phi(T.dims, idx, T.vals, fs, np.ones((4, 2)), 0)
+
+
+@pytest.mark.parametrize("inner", [1, 3])
+def test_mu_two_way_is_kl_nmf(oracle, inner):
+    """With N = 2 the MU loop is the Lee-Seung multiplicative update of
+    non-negative matrix factorisation under the KL divergence, X ~ W H^T:
+    with H's columns summing to one, W <- W * ((X / (W H^T)) H), then the
+    column sums of W move into lambda, and the same for H with X^T.  Written
+    here with plain dense matrix products (tol = 0: every inner iteration
+    updates; one outer iteration, so no shift S)."""
+    dims, R = (7, 5), 3
+    T = synth.random_tensor(dims, 25, R, 31)
+    X = np.zeros(dims)
+    np.add.at(X, (T.idx[0], T.idx[1]), T.vals)
+    A = [a / a.sum(axis=0, keepdims=True) for a in synth.random_factors(dims, R, 32)]
+    lam = np.array([2.0, 5.0, 3.5])
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, A, tol=0.0, max_outer=1, max_inner=inner, kappa=0.0)
+    W, H = A[0] * lam, A[1]
+    for _ in range(inner):
+        W = W * ((X / np.maximum(W @ H.T, EPS)) @ H)
+    lam1 = W.sum(axis=0)
+    A0 = W / lam1
+    H = A[1] * lam1
+    for _ in range(inner):
+        H = H * ((X.T / np.maximum(H @ A0.T, EPS)) @ A0)
+    lam2 = H.sum(axis=0)
+    np.testing.assert_allclose(ref["lambda"], lam2, rtol=1e-12)
+    np.testing.assert_allclose(ref["factors"][0], A0, rtol=1e-12)
+    np.testing.assert_allclose(ref["factors"][1], H / lam2, rtol=1e-12)
