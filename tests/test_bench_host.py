@@ -107,3 +107,20 @@ def test_roofline_line_is_strict_json():
     assert r["traffic"] is not None and 2.7e9 < r["traffic"] < 2.9e9
     assert r["paper_model"]["words_per_nonzero"] == 162
     assert abs(r["paper_model"]["achieved"] - 30 * 1e7 * 162 * 8 / 43.6e-3 / 1e9) < 1e-6
+
+
+def test_batch_workload_specs():
+    """The 64-tensor batch: 3-way, dims within [50,50,50]-[20000,20000,500],
+    nnz within [1e3, 1e6] and at most 10% of the coordinate space, R from
+    {8, 16, 32}, every tensor seeded differently; the same specs on every call."""
+    from paper_2307_03276_gb300 import synth
+    specs = synth.batch_specs()
+    assert len(specs) == 64 and specs == synth.batch_specs()
+    assert len({s.seed for s in specs}) == 64
+    for s in specs:
+        assert len(s.dims) == 3
+        assert all(lo <= d <= hi for d, lo, hi in zip(s.dims, (50, 50, 50), (20_000, 20_000, 500)))
+        assert s.nnz <= 0.1 * s.dims[0] * s.dims[1] * s.dims[2] + 1
+        assert s.nnz <= 1_000_000 and (s.nnz >= 1_000 or s.nnz >= int(0.1 * s.dims[0] * s.dims[1] * s.dims[2]))
+        assert s.rank in (8, 16, 32)
+    assert {s.rank for s in specs} == {8, 16, 32}
