@@ -245,3 +245,35 @@ def test_mu_two_way_is_kl_nmf(oracle, inner):
     np.testing.assert_allclose(ref["lambda"], lam2, rtol=1e-12)
     np.testing.assert_allclose(ref["factors"][0], A0, rtol=1e-12)
     np.testing.assert_allclose(ref["factors"][1], H / lam2, rtol=1e-12)
+
+
+def _golden():
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("make_golden", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_c1_golden_trajectory(oracle):
+    """The oracle's ten-outer-iteration solve of the 100 x 80 x 60 workload
+    reproduces the trajectory stored in tests/golden/c1_mu_oracle.txt
+    (written by make_golden.py from the oracle alone): inner iterations per
+    mode, KKT violation and log-likelihood per outer iteration, and lambda,
+    whose sum is the total count (mass conservation)."""
+    g = _golden()
+    want = g.read()
+    r = g.solve()
+    assert r["outer_iters"] == want["outer_iters"] and bool(r["converged"]) == want["converged"]
+    for k, (inner, kkt, ll) in enumerate(want["outer"]):
+        assert list(r["inner"][k]) == inner
+        assert abs(r["kkt"][k] - kkt) <= 1e-13 * kkt
+        assert abs(r["loglik"][k] - ll) <= 1e-13 * abs(ll)
+    np.testing.assert_allclose(r["lambda"], want["lambda"], rtol=1e-13)
+    T = synth.generate(synth.C1)
+    assert abs(want["lambda"].sum() - T.vals.sum()) <= 1e-12 * T.vals.sum()
+    # the log-likelihood never decreases along the stored trajectory (kappa's shift aside, MU is an MM method)
+    lls = [o[2] for o in want["outer"]]
+    assert all(b >= a for a, b in zip(lls, lls[1:]))
