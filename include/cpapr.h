@@ -135,7 +135,10 @@ void cpapr_default_options(cpapr_options *opt);
  *  rank    R >= 1.   opt  NULL for defaults.   out  receives the context.
  * The tensor is copied to the device and sorted once per mode (the per-mode
  * ordering of the paper's Section "CP-APR MU Implementation and
- * Parallelization": sorting each mode once at the start).
+ * Parallelization": sorting each mode once at the start).  idx and vals may
+ * be host memory (pageable or pinned: copied by the copy engines, pinned
+ * being faster) or device memory (read in place); the call returns after the
+ * inputs are no longer used.
  * Errors: E_ARG, E_RANGE (coordinate out of range), E_VALUE, E_NOMEM, E_CUDA.
  * On error *out is NULL and the message is available from
  * cpapr_last_error(NULL) on the calling thread.
