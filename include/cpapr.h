@@ -200,14 +200,16 @@ cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *ou
  * allocate device memory during the call: for example code whose device
  * memory is held by another allocator (a framework's caching allocator that
  * has reserved the GPU, a fixed memory budget) or a loop that must not block
- * on cudaMalloc/cudaFree.  The paper has no counterpart; it is a deployment
- * variant of Algorithm 2.
+ * on cudaMalloc/cudaFree.  The paper has no counterpart.
  *  B    NULL (B = A^(mode) diag(lambda)) or a DEVICE pointer, I_mode x R doubles.
  *  out  DEVICE pointer receiving I_mode x R doubles.
  * The kernel's scratch (per-tile partial rows, 2 x tiles x padded rank
  * elements) comes from a fixed array of CPAPR_NOALLOC_SCRATCH_BYTES in device
  * memory that every GPU loading the library holds until the process exits;
- * the call performs no cudaMalloc, cudaFree or other allocating call.
+ * the call performs no cudaMalloc, cudaFree or other allocating call.  It
+ * runs on the context's device (made current for the call; the caller's
+ * current device is restored before it returns) and synchronises the
+ * context's stream before returning.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents
@@ -216,7 +218,8 @@ cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *ou
  * by the caller.
  * Errors: E_RANGE when the mode needs more scratch than the array holds
  * (raise tile_nnz or use cpapr_phi), E_ARG for host pointers or a bad mode,
- * E_STATE without a model, E_CUDA.
+ * E_STATE without a model, E_TIMEOUT when a bounded device-side wait gave up
+ * (out is then incomplete; the context stays usable), E_CUDA.
  */
 cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const double *B, double *out);
 
@@ -256,11 +259,14 @@ typedef struct {
  * max_outer = 2 (S is applied from the second outer iteration on).
  * inner_trace (NULL or max_outer * N int32) receives the inner iterations
  * of each (outer, mode); ll_trace (NULL or max_outer doubles) receives the
- * log-likelihood after each outer iteration (costs one pass per iteration).
+ * log-likelihood after each outer iteration (costs one pass per iteration);
+ * kkt_trace (NULL or max_outer doubles) receives, per outer iteration, the
+ * largest last-checked violation max|min(B, 1 - Phi)| over the modes (free:
+ * the host reads the inner-loop states once per outer iteration anyway).
  * Errors: E_ARG, E_STATE (no model), E_CUDA.
  */
 cpapr_status cpapr_mu_solve(cpapr_ctx *ctx, double tol, int32_t max_outer, int32_t max_inner, cpapr_result *res,
-                            int32_t *inner_trace, double *ll_trace);
+                            int32_t *inner_trace, double *ll_trace, double *kkt_trace);
 
 /*
  * Solves `count` independent contexts (each with its own tensor, rank and

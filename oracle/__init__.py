@@ -8,6 +8,7 @@ the same bits) and wraps it with ctypes.
 
 Functions follow the paper (arXiv 2307.03276):
   phi      -- Algorithm 2 evaluated per nonzero as in Algorithm 3
+  phi_threads -- the same on several host threads (the CPU baseline's timing)
   mttkrp   -- the unit-denominator variant (Experiment 8, MTTKRP)
   loglik   -- Poisson log-likelihood of the Kruskal model (not in the paper)
   mu_solve -- Algorithm 1 with the readings listed in cpapr_oracle.c
@@ -34,7 +35,7 @@ def build(force: bool = False) -> str:
     """Compiles liboracle.so next to the source (no-op when up to date)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
                                "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -49,6 +50,8 @@ def _load():
         i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
         lib.oracle_phi.argtypes = [i32, P, i64, P, P, i32, P, P, i32, f64, i32, P]
         lib.oracle_phi.restype = i32
+        lib.oracle_phi_threads.argtypes = [i32, P, i64, P, P, i32, P, P, i32, f64, i32, P, i32]
+        lib.oracle_phi_threads.restype = i32
         lib.oracle_loglik.argtypes = [i32, P, i64, P, P, i32, P, P]
         lib.oracle_loglik.restype = f64
         lib.oracle_mu_solve.argtypes = [i32, P, i64, P, P, i32, P, P, f64, i32, i32, f64, f64, f64,
@@ -115,6 +118,25 @@ def _phi_or_mttkrp(dims, idx, vals, factors, B, mode, eps, unit):
                         _ptr(B), int(mode), float(eps), int(unit), _ptr(out))
     if rc != 0:
         raise ValueError(f"oracle_phi failed with code {rc}")
+    return out
+
+
+def phi_threads(dims, idx, vals, factors, B, mode: int, nthreads: int, eps: float = EPS) -> np.ndarray:
+    """The same Phi^(mode) on `nthreads` host threads, each owning a range of
+    rows of Phi (about nnz / nthreads nonzeros each) and summing them exactly
+    as phi() does: the CPU baseline on all cores.  Bit-for-bit equal to phi()."""
+    lib = _load()
+    dims, idx, vals = _coo(dims, idx, vals)
+    R = np.asarray(factors[0]).shape[1]
+    fs = _factors(factors, dims, R)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.shape != (int(dims[mode]), R):
+        raise ValueError("B must be I_n x R")
+    out = np.zeros((int(dims[mode]), R))
+    rc = lib.oracle_phi_threads(len(dims), _ptr(dims), vals.shape[0], _ptr(idx), _ptr(vals), R, _ptr_array(fs),
+                                _ptr(B), int(mode), float(eps), 0, _ptr(out), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_phi_threads failed with code {rc}")
     return out
 
 

@@ -31,6 +31,7 @@
  *    Poisson log-likelihood without the constant sum log(x!).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -119,6 +120,129 @@ int oracle_phi(int N, const int64_t *dims, int64_t nnz, const int64_t *idx, cons
         Phi[e] += comp[e];
     free(comp);
     free(pi);
+    return ORACLE_OK;
+}
+
+/*
+ * The same Phi^(n) (or MTTKRP) on several host threads, for timing the CPU
+ * baseline on all of a machine's cores.  Thread t owns the rows
+ * [row0, row1) of Phi^(n), a range holding about nnz / nthreads nonzeros;
+ * it visits every nonzero in the given order and evaluates those whose
+ * mode-n coordinate falls in its rows exactly as oracle_phi does.  Each row
+ * is therefore summed by one thread, term by term in the same order and with
+ * the same Neumaier compensation as oracle_phi: the result is bit-for-bit
+ * oracle_phi's, with no per-thread copies of Phi to merge.
+ */
+struct phi_rows {
+    int N;
+    const int64_t *dims;
+    int64_t nnz;
+    const int64_t *idx;
+    const double *vals;
+    int R;
+    const double *const *A;
+    const double *B;
+    int n;
+    double eps;
+    int unit_denominator;
+    int64_t row0, row1;  /* rows of Phi this thread owns */
+    double *Phi, *comp;  /* I_n x R values and compensations (shared, disjoint rows) */
+};
+
+static void *phi_rows_run(void *arg)
+{
+    struct phi_rows *c = (struct phi_rows *)arg;
+    const int R = c->R, n = c->n;
+    double pi[256];  /* R <= 256 (checked by the caller) */
+    for (int64_t j = 0; j < c->nnz; ++j) {
+        int64_t i = c->idx[(int64_t)n * c->nnz + j];
+        if (i < c->row0 || i >= c->row1)
+            continue;
+        for (int r = 0; r < R; ++r)
+            pi[r] = 1.0;
+        for (int m = 0; m < c->N; ++m) {
+            if (m == n)
+                continue;
+            const double *row = c->A[m] + c->idx[(int64_t)m * c->nnz + j] * R;
+            for (int r = 0; r < R; ++r)
+                pi[r] *= row[r];
+        }
+        double v = c->vals[j];
+        if (!c->unit_denominator) {
+            double s = 0.0;
+            for (int r = 0; r < R; ++r)
+                s += c->B[i * R + r] * pi[r];
+            v = c->vals[j] / (s > c->eps ? s : c->eps);
+        }
+        for (int r = 0; r < R; ++r)
+            nsum_add(&c->Phi[i * R + r], &c->comp[i * R + r], v * pi[r]);
+    }
+    for (int64_t e = c->row0 * R; e < c->row1 * R; ++e)
+        c->Phi[e] += c->comp[e];
+    return NULL;
+}
+
+int oracle_phi_threads(int N, const int64_t *dims, int64_t nnz, const int64_t *idx, const double *vals,
+                       int R, const double *const *A, const double *B, int n, double eps,
+                       int unit_denominator, double *Phi, int nthreads)
+{
+    if (N < 2 || R < 1 || R > 256 || n < 0 || n >= N || nnz < 0 || nthreads < 1)
+        return ORACLE_E_ARG;
+    if (check_coords(N, dims, nnz, idx))
+        return ORACLE_E_RANGE;
+    const int64_t In = dims[n];
+    struct phi_rows *ch = calloc((size_t)nthreads, sizeof(struct phi_rows));
+    pthread_t *th = calloc((size_t)nthreads, sizeof(pthread_t));
+    char *running = calloc((size_t)nthreads, 1);
+    int64_t *count = calloc((size_t)In + 1, sizeof(int64_t));
+    double *comp = calloc((size_t)In * R + 1, sizeof(double));
+    if (!ch || !th || !running || !count || !comp) {
+        free(ch);
+        free(th);
+        free(running);
+        free(count);
+        free(comp);
+        return ORACLE_E_NOMEM;
+    }
+    memset(Phi, 0, sizeof(double) * (size_t)In * R);
+    /* row ranges of about nnz / nthreads nonzeros each */
+    for (int64_t j = 0; j < nnz; ++j)
+        count[idx[(int64_t)n * nnz + j]] += 1;
+    int64_t row = 0, seen = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        struct phi_rows *c = &ch[t];
+        c->N = N;
+        c->dims = dims;
+        c->nnz = nnz;
+        c->idx = idx;
+        c->vals = vals;
+        c->R = R;
+        c->A = A;
+        c->B = B;
+        c->n = n;
+        c->eps = eps;
+        c->unit_denominator = unit_denominator;
+        c->Phi = Phi;
+        c->comp = comp;
+        c->row0 = row;
+        const int64_t target = nnz * (t + 1) / nthreads;
+        while (row < In && (seen < target || t == nthreads - 1))
+            seen += count[row++];
+        c->row1 = row;
+    }
+    for (int t = 1; t < nthreads; ++t)
+        running[t] = pthread_create(&th[t], NULL, phi_rows_run, &ch[t]) == 0;
+    for (int t = 0; t < nthreads; ++t)
+        if (!running[t])
+            phi_rows_run(&ch[t]);  /* range 0, and any range no thread could take */
+    for (int t = 1; t < nthreads; ++t)
+        if (running[t])
+            pthread_join(th[t], NULL);
+    free(ch);
+    free(th);
+    free(running);
+    free(count);
+    free(comp);
     return ORACLE_OK;
 }
 

@@ -89,7 +89,7 @@ def load() -> ctypes.CDLL:
     lib.cpapr_set_state.argtypes = [P, P, P, P, i64]
     lib.cpapr_mttkrp.argtypes = [P, i32, P]
     lib.cpapr_loglik.argtypes = [P, P]
-    lib.cpapr_mu_solve.argtypes = [P, f64, i32, i32, ctypes.POINTER(Result), P, P]
+    lib.cpapr_mu_solve.argtypes = [P, f64, i32, i32, ctypes.POINTER(Result), P, P, P]
     lib.cpapr_batch_mu_solve.argtypes = [P, i32, f64, i32, i32, P]
     lib.cpapr_get_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.cpapr_kernel_stats.argtypes = [P, i32, ctypes.POINTER(i64), ctypes.POINTER(f64), i32]
@@ -268,20 +268,23 @@ def cpapr_loglik(ctx) -> float:
 
 
 def cpapr_mu_solve(ctx, tol=1e-4, max_outer=10, max_inner=10, trace=False, ll_trace=None) -> dict:
-    """trace: also return the inner iterations per (outer, mode) and, unless
-    ll_trace is False, the log-likelihood after every outer iteration."""
+    """trace: also return the inner iterations per (outer, mode), the KKT
+    violation of every outer iteration and, unless ll_trace is False, the
+    log-likelihood after every outer iteration."""
     if ll_trace is None:
         ll_trace = trace
     res = Result()
     info = cpapr_get_info(ctx) if trace else None
     inner = np.zeros(max(max_outer, 1) * (info.nmodes if info else 1), dtype=np.int32) if trace else None
+    kkt = np.zeros(max(max_outer, 1)) if trace else None
     ll = np.zeros(max(max_outer, 1)) if ll_trace else None
     _check(load().cpapr_mu_solve(ctx, float(tol), int(max_outer), int(max_inner), ctypes.byref(res), _ptr(inner),
-                                 _ptr(ll)), ctx)
+                                 _ptr(ll), _ptr(kkt)), ctx)
     out = res.as_dict()
     k = res.outer_iters
     if trace:
         out["inner"] = inner[:k * info.nmodes].reshape(k, info.nmodes)
+        out["kkt_trace"] = kkt[:k]
     if ll_trace:
         out["loglik_trace"] = ll[:k]
     return out

@@ -660,12 +660,12 @@ cpapr_status cpapr_loglik(cpapr_ctx *ctx, double *out) {
 }
 
 cpapr_status cpapr_mu_solve(cpapr_ctx *ctx, double tol, int32_t max_outer, int32_t max_inner, cpapr_result *res,
-                            int32_t *inner_trace, double *ll_trace) {
+                            int32_t *inner_trace, double *ll_trace, double *kkt_trace) {
     API_ENTER(ctx);
     if (!res) return fail(ctx, CPAPR_E_ARG, "res is NULL");
     if (max_outer < 0 || max_inner < 1 || !(tol >= 0.0)) return fail(ctx, CPAPR_E_ARG, "bad tol / iteration bounds");
     if (!ctx->model_set) return fail(ctx, CPAPR_E_STATE, "no model set");
-    CPAPR_TRY(mu_solve(ctx, tol, max_outer, max_inner, res, inner_trace, ll_trace));
+    CPAPR_TRY(mu_solve(ctx, tol, max_outer, max_inner, res, inner_trace, ll_trace, kkt_trace));
     return check_waits(ctx);
 }
 

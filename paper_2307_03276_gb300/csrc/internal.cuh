@@ -214,7 +214,7 @@ cpapr_status exclusive_scan_u32(cpapr_ctx *ctx, uint32_t *data, int64_t n, uint3
 
 // ---- solver (solver.cu) -------------------------------------------------------
 cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, cpapr_result *res,
-                      int32_t *inner_trace, double *ll_trace);
+                      int32_t *inner_trace, double *ll_trace, double *kkt_trace);
 cpapr_status batch_mu_solve(cpapr_ctx *const *ctxs, int count, double tol, int max_outer, int max_inner,
                             cpapr_result *results);
 

@@ -15,9 +15,11 @@
 // CPAPR_NOALLOC_SCRATCH_BYTES bytes: every GPU that loads the library holds it
 // until the process exits.  In host code its name is only a host-side stand-in,
 // so the device address is looked up with cudaGetSymbolAddress, once per
-// device, by the first call made while that device is current.
+// device, by the first call on a context of that device (with the context's
+// device made current for the call and the caller's device restored after).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -36,20 +38,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-cpapr_status scratch_address(cpapr_ctx *ctx, void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(ctx, CPAPR_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev != ctx->device) {
-        e = cudaSetDevice(ctx->device);
-        if (e != cudaSuccess) return fail(ctx, CPAPR_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-        dev = ctx->device;
+// Makes ctx->device current for the lifetime of the guard and puts the
+// caller's device back afterwards, on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+        else if (err == cudaSuccess) prev = -1;  // already current: nothing to restore
     }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Device address of the scratch array on ctx->device (which the caller has
+// made current), looked up once per device.
+cpapr_status scratch_address(cpapr_ctx *ctx, void **out) {
+    const int dev = ctx->device;
     if (dev < 0 || dev >= kMaxDevices) return fail(ctx, CPAPR_E_ARG, "device ordinal too large");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(ctx, CPAPR_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
@@ -84,6 +96,9 @@ extern "C" cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const do
                         std::to_string(L.ntiles) + " tiles x " + std::to_string(ctx->Rp) +
                         " ranks); the fixed scratch holds " + std::to_string((long long)CPAPR_NOALLOC_SCRATCH_BYTES) +
                         ": use cpapr_phi, or a larger tile_nnz");
+    DeviceGuard guard(ctx->device);
+    if (guard.err != cudaSuccess)
+        return fail(ctx, CPAPR_E_CUDA, std::string("selecting the context's device: ") + cudaGetErrorString(guard.err));
     void *scratch = nullptr;
     CPAPR_TRY(scratch_address(ctx, &scratch));
     if (ctx->nnz == 0) {
@@ -101,6 +116,20 @@ extern "C" cpapr_status cpapr_phi_noalloc(cpapr_ctx *ctx, int32_t mode, const do
         CPAPR_TRY(launch_phi_given_carry(ctx, mode, ctx->B, ctx->outbuf, scratch));
         CPAPR_TRY(download_matrix(ctx, ctx->outbuf, ctx->dims[mode], out));
     }
+    // Did a tile's bounded staging wait give up?  Such a tile never wrote its
+    // rows nor counted its partials: clear the flag and every mode's
+    // partial counters (plain memsets, no allocation) and report it.
+    int32_t waited_out = 0;
+    CPAPR_CUDA(ctx, cudaMemcpyAsync(&waited_out, ctx->errflag + 3, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (waited_out) {
+        CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag + 3, 0, 4, ctx->stream));
+        for (int n = 0; n < ctx->N; ++n)
+            if (ctx->mode[n].splitcnt)
+                CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->mode[n].splitcnt, 0,
+                                                (size_t)std::max(ctx->mode[n].nsplit, 1) * 4, ctx->stream));
+        CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, CPAPR_E_TIMEOUT, "a device-side staging wait gave up; out is incomplete");
+    }
     return CPAPR_OK;
 }

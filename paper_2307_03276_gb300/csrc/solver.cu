@@ -123,7 +123,7 @@ cpapr_status batch_mu_solve_persistent(cpapr_ctx *const *ctxs, int count, double
                                        cpapr_result *results);
 
 cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, cpapr_result *res,
-                      int32_t *inner_trace, double *ll_trace) {
+                      int32_t *inner_trace, double *ll_trace, double *kkt_trace) {
     const int N = ctx->N;
     std::vector<InnerState> hs(N);
     int outer = 0, total_inner = 0;
@@ -147,6 +147,7 @@ cpapr_status mu_solve(cpapr_ctx *ctx, double tol, int max_outer, int max_inner, 
             if (inner_trace) inner_trace[(int64_t)k * N + n] = hs[n].used;
         }
         kkt_last = kmax;
+        if (kkt_trace) kkt_trace[k] = kmax;
         if (ll_trace) CPAPR_TRY(loglik_now(ctx, &ll_trace[k]));
         if (all_first) {
             conv = true;

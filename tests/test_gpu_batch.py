@@ -125,3 +125,69 @@ def test_batch_with_an_empty_tensor(precision):
         ll = t.loglik()
         assert np.isfinite(r["loglik"]) and abs(r["loglik"] - ll) <= 1e-12 * max(1.0, abs(ll))
         t.close()
+
+
+def _sample_rows(T, n, k=4):
+    counts = np.bincount(T.idx[n], minlength=T.dims[n])
+    nonempty = np.flatnonzero(counts)
+    rng = np.random.default_rng(n + 300)
+    rows = {int(np.argmax(counts)), int(nonempty[np.argmin(counts[nonempty])])}
+    rows.update(int(r) for r in rng.choice(nonempty, size=min(k, nonempty.size), replace=False))
+    return np.array(sorted(rows))
+
+
+def _rel(got, want):
+    nz = want != 0
+    e = np.zeros_like(want)
+    e[nz] = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+    e[~nz] = np.abs(got[~nz]) > 0
+    return float(e.max())
+
+
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_full_64_tensor_batch_equals_individual_solves(precision):
+    """The 64-tensor batch at its full size (dims log-uniform up to
+    20000 x 20000 x 500, 1e3..1e6 nonzeros, R from {8, 16, 32}): two outer
+    iterations through the persistent batched solver against one mu_solve
+    per tensor from the same start (same inner iteration counts; lambda and
+    factors equal up to the order of the column sums), and sampled Phi rows
+    of the final models of the three largest tensors against the oracle."""
+    Ts = [synth.generate(sp) for sp in synth.batch_specs(count=64)]
+    ms = models(Ts)
+    tol, mo, mi = 1e-4, 2, 10
+    fp64 = precision == cpapr.CPAPR_FP64
+    batch = [cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) for T in Ts]
+    for t, (lam, fs) in zip(batch, ms):
+        t.set_model(lam, fs)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in batch], tol, mo, mi)
+    largest = sorted(range(len(Ts)), key=lambda i: -Ts[i].nnz)[:3]
+    for i, (T, t, (lam, fs), r) in enumerate(zip(Ts, batch, ms, res)):
+        lb, fb = t.get_model()
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision) as s:
+            s.set_model(lam, fs)
+            ri = s.mu_solve(tol, mo, mi)
+            li, fi = s.get_model()
+        assert (r["outer_iters"], r["total_inner"]) == (ri["outer_iters"], ri["total_inner"]), i
+        if fp64:
+            np.testing.assert_allclose(lb, li, rtol=1e-12)
+            for a, b in zip(fb, fi):
+                np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-15 * b.max())
+            assert abs(r["loglik"] - ri["loglik"]) <= 1e-12 * abs(ri["loglik"])
+        else:
+            # FP32 factors: the batched column sums round differently in the
+            # last FP64 bits, which can move an FP32 factor entry by one ulp
+            np.testing.assert_allclose(lb, li, rtol=1e-5)
+            for a, b in zip(fb, fi):
+                np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-7 * b.max())
+            assert abs(r["loglik"] - ri["loglik"]) <= 1e-5 * abs(ri["loglik"])
+        if i in largest:
+            # Phi of the final batched model, sampled rows against the oracle
+            for n in range(T.nmodes):
+                rows = _sample_rows(T, n)
+                mask = np.isin(T.idx[n], rows)
+                idx = np.ascontiguousarray(T.idx[:, mask])
+                vals = np.ascontiguousarray(T.vals[mask])
+                want = oracle.phi(T.dims, idx, vals, fb, fb[n] * lb[None, :], n)[rows]
+                got = t.phi(n)[rows]
+                assert _rel(got, want) <= (1e-12 if fp64 else 1e-5), (i, n)
+        t.close()

@@ -645,3 +645,37 @@ def test_create_from_pinned_and_device_inputs(where):
     with pytest.raises(cpapr.CpaprError) as e:
         cpapr.Tensor(T.dims, [bad[m] for m in range(T.nmodes)], val_t, T.rank)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_mu_shift_moves_an_inadmissible_zero(precision):
+    """Algorithm 1's B <- (A + S) Lambda with Chi and Kolda's shift: a factor
+    entry set to exactly 0 stays 0 under B <- B * Phi; from the second outer
+    iteration on, S adds kappa where A < kappa_tol and the previous Phi > 1,
+    which moves it.  Same tiny tensor and model as the oracle's dense pin,
+    three outer iterations against the oracle (FP64 at the MU-solve
+    tolerances of these tests, FP32 at the FP32 ones)."""
+    T = synth.random_tensor((5, 4, 3), 35, 3, 101)
+    fs = synth.random_factors(T.dims, 3, 108)
+    fs[0][1, 0] = 0.0
+    lam = np.ones(3)
+    kappa = 0.01
+    ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-12, max_outer=3, max_inner=4, kappa=kappa)
+    assert ref["factors"][0][1, 0] > 0.0
+    with cpapr.Tensor(T.dims, T.idx, T.vals, 3, precision=precision, kappa=kappa, tile_nnz=64) as t:
+        t.set_model(lam, fs)
+        r1 = t.mu_solve(tol=1e-12, max_outer=1, max_inner=4, trace=True, ll_trace=False)
+        assert t.get_model()[1][0][1, 0] == 0.0  # no shift in the first outer iteration
+        r2 = t.mu_solve(tol=1e-12, max_outer=2, max_inner=4, trace=True, ll_trace=False)
+        lg, fg = t.get_model()
+    assert fg[0][1, 0] > 0.0
+    inner = np.concatenate([r1["inner"], r2["inner"]]).tolist()
+    assert inner == ref["inner"].tolist()
+    if precision == cpapr.CPAPR_FP64:
+        np.testing.assert_allclose(lg, ref["lambda"], rtol=1e-10)
+        for A, Ar in zip(fg, ref["factors"]):
+            np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
+    else:
+        np.testing.assert_allclose(lg, ref["lambda"], rtol=1e-5)
+        for A, Ar in zip(fg, ref["factors"]):
+            np.testing.assert_allclose(A, Ar, rtol=1e-4, atol=1e-6 * Ar.max())

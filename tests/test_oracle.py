@@ -277,3 +277,18 @@ def test_c1_golden_trajectory(oracle):
     # the log-likelihood never decreases along the stored trajectory (kappa's shift aside, MU is an MM method)
     lls = [o[2] for o in want["outer"]]
     assert all(b >= a for a, b in zip(lls, lls[1:]))
+
+
+@pytest.mark.parametrize("nthreads", [1, 3, 8, 64])
+def test_threaded_phi_equals_single_threaded(oracle, nthreads):
+    """The multi-threaded Phi of the CPU baseline (each thread owns a range of
+    rows and sums them term by term in the given order) gives the plain
+    oracle's bits: rows with thousands of terms, a skewed row, empty rows,
+    more threads than a mode has rows."""
+    T = synth.generate(synth.scaled(synth.C2, 20_000, dims=(300, 200, 50), rank=7))
+    fs = synth.random_factors(T.dims, 7, 5)
+    for n in range(3):
+        B = fs[n] * 1.3
+        want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n)
+        got = oracle.phi_threads(T.dims, T.idx, T.vals, fs, B, n, nthreads)
+        assert np.array_equal(got, want)
