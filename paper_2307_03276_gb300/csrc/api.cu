@@ -468,6 +468,17 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
             cudaMemsetAsync(ctx->Phi[m], 0, (size_t)dims[m] * Rp * ctx->esize, ctx->stream) != cudaSuccess)
             return bail(fail(ctx, CPAPR_E_CUDA, "memset"));
     }
+    if (ctx->esize == 4) {
+        // FP64 masters of the factors and of B (see cpapr_ctx::A64)
+        size_t mofs[CPAPR_MAX_MODES + 1] = {};
+        for (int m = 0; m < nmodes; ++m) mofs[m + 1] = mofs[m] + (((size_t)dims[m] * Rp * 8 + 255) & ~(size_t)255);
+        CR_TRY(dev_alloc(ctx, &p, mofs[nmodes]));
+        if (cudaMemsetAsync(p, 0, mofs[nmodes], ctx->stream) != cudaSuccess)
+            return bail(fail(ctx, CPAPR_E_CUDA, "memset"));
+        for (int m = 0; m < nmodes; ++m) ctx->A64[m] = (double *)((char *)p + mofs[m]);
+        CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * 8));
+        ctx->B64 = (double *)p;
+    }
     CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * ctx->esize));
     ctx->B = p;
     CR_TRY(dev_alloc(ctx, &p, (size_t)ctx->Imax * Rp * ctx->esize));
@@ -513,7 +524,7 @@ cpapr_status cpapr_set_model(cpapr_ctx *ctx, const double *lambda, const double 
     CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->errflag, 0, 16, ctx->stream));
     CPAPR_CUDA(ctx, cudaMemcpyAsync(ctx->lambda, hl.data(), (size_t)ctx->Rp * 8, cudaMemcpyHostToDevice, ctx->stream));
     for (int m = 0; m < ctx->N; ++m) {
-        CPAPR_TRY(upload_matrix(ctx, factors[m], ctx->dims[m], ctx->A[m]));
+        CPAPR_TRY(upload_factor(ctx, m, factors[m]));
         CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->Phi[m], 0, (size_t)ctx->dims[m] * ctx->Rp * ctx->esize, ctx->stream));
     }
     int32_t flags[4] = {0, 0, 0, 0};
@@ -548,7 +559,13 @@ cpapr_status cpapr_get_model(cpapr_ctx *ctx, double *lambda, double *const *fact
     if (factors)
         for (int m = 0; m < ctx->N; ++m) {
             if (!factors[m]) continue;
-            CPAPR_TRY(download_matrix(ctx, ctx->A[m], ctx->dims[m], factors[m]));
+            // the FP32 form returns the FP64 masters (what the MU loop keeps)
+            if (ctx->A64[m])
+                CPAPR_CUDA(ctx, cudaMemcpy2DAsync(factors[m], (size_t)ctx->R * 8, ctx->A64[m], (size_t)ctx->Rp * 8,
+                                                  (size_t)ctx->R * 8, (size_t)ctx->dims[m], cudaMemcpyDefault,
+                                                  ctx->stream));
+            else
+                CPAPR_TRY(download_matrix(ctx, ctx->A[m], ctx->dims[m], factors[m]));
             // download_matrix stages FP32 through ctx->stage: finish before reuse
             CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         }

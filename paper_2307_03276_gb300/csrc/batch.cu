@@ -43,6 +43,8 @@ struct BatchTensor {
     int32_t rp;
     int64_t rows;        // I_n
     void *A;             // A^(n)
+    double *Am;          // FP32 form: FP64 masters of A^(n) and of B (else null)
+    double *Bm;
     double *lambda;
     double *colpart;     // [nchunks][rp] column-sum partials
     int32_t chunk0, nchunks;
@@ -204,9 +206,11 @@ __global__ void __launch_bounds__(256) batch_sb_kernel(const BatchTensor *__rest
     const T *P = reinterpret_cast<const T *>(d.a.out);
     T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
     for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
-        const double a = (double)A[e];
+        const double a = d.Am ? d.Am[e] : (double)A[e];
         const double s = (shift && a < d.kappa_tol && (double)P[e] > 1.0) ? d.kappa : 0.0;
-        B[e] = (T)((a + s) * d.lambda[e & (Rp - 1)]);  // Rp is a power of two
+        const double b = (a + s) * d.lambda[e & (Rp - 1)];  // Rp is a power of two
+        if (d.Bm) d.Bm[e] = b;
+        B[e] = (T)b;
     }
 }
 
@@ -257,7 +261,12 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__
         constexpr int W = Vec16<T>::n;
         V *B = reinterpret_cast<V *>(const_cast<void *>(d.a.B));
         const V *P = reinterpret_cast<const V *>(d.a.out);
-        for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x) B[e] = vmul(B[e], P[e]);
+        if (d.Bm) {
+            for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x)
+                B[e] = master_mul(d.Bm, P[e], e);
+        } else {
+            for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x) B[e] = vmul(B[e], P[e]);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -311,7 +320,7 @@ __global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchTensor *__
     const T *B = reinterpret_cast<const T *>(d.a.B);
     double s = 0.0;
     if (rl < nrl)
-        for (int64_t i = r0 + rl; i < r1; i += nrl) s += (double)B[i * Rp + c];
+        for (int64_t i = r0 + rl; i < r1; i += nrl) s += d.Bm ? d.Bm[i * Rp + c] : (double)B[i * Rp + c];
     sm[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < Rp) {
@@ -357,7 +366,12 @@ __global__ void __launch_bounds__(256) batch_scale_kernel(const BatchTensor *__r
     for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
         const int c = (int)(e & (Rp - 1));  // Rp is a power of two
         const double l = lam[c];
-        if (l > 0.0) A[e] = (T)(inv[c] != 0.0 ? (double)B[e] * inv[c] : (double)B[e] / l);
+        if (l > 0.0) {
+            const double b = d.Bm ? d.Bm[e] : (double)B[e];
+            const double v = inv[c] != 0.0 ? b * inv[c] : b / l;
+            if (d.Am) d.Am[e] = v;
+            A[e] = (T)v;
+        }
     }
 }
 
@@ -373,8 +387,11 @@ __global__ void __launch_bounds__(256) batch_scale_b_kernel(const BatchTensor *_
     const int64_t r1 = min(r0 + kChunkRows, d.rows);
     const T *A = reinterpret_cast<const T *>(d.A);
     T *B = reinterpret_cast<T *>(const_cast<void *>(d.a.B));
-    for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x)
-        B[e] = (T)((double)A[e] * d.lambda[e & (Rp - 1)]);
+    for (int64_t e = r0 * Rp + threadIdx.x; e < r1 * Rp; e += blockDim.x) {
+        const double b = (d.Am ? d.Am[e] : (double)A[e]) * d.lambda[e & (Rp - 1)];
+        if (d.Bm) d.Bm[e] = b;
+        B[e] = (T)b;
+    }
 }
 
 // Every tensor's log-likelihood total: item (t, b) is block b of tensor t's
@@ -660,8 +677,10 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
                 if (m == n) continue;
                 a.idx[k] = L.idx[k];
                 a.A[k] = c->A[m];
+                a.Am[k] = c->A64[m];
                 ++k;
             }
+            a.Bm = c->B64;
             a.val = L.val;
             a.B = c->B;
             a.out = c->Phi[n];
@@ -685,6 +704,8 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             d.rp = c->Rp;
             d.rows = c->dims[n];
             d.A = c->A[n];
+            d.Am = c->A64[n];
+            d.Bm = c->B64;
             d.lambda = c->lambda;
             d.colpart = P.colpart + colpart_off[i];
             d.nchunks = (int32_t)ceil_div(c->dims[n], kChunkRows);
@@ -853,7 +874,8 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && m0.ntiles > 0) e = launch_ll_batch<T>(P, N - 1, grid, s);
         if (e == cudaSuccess) {
-            batch_ll_total_kernel<T><<<P.nllitems, 256, 0, s>>>(P.llargs, P.llitems);
+            // the column sums of the totals run on the FP64 factors (masters in the FP32 form)
+            batch_ll_total_kernel<double><<<P.nllitems, 256, 0, s>>>(P.llargs, P.llitems);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)

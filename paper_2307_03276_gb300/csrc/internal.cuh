@@ -10,7 +10,10 @@
 //     tile table  row_first[t], the rows that span tiles, each tile's
 //                 split of its head and tail partial, per-split counters
 //   model:  A[m] T [I_m x Rp], lambda double [Rp], B T [Imax x Rp],
-//           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration)
+//           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration);
+//           FP32 form: also FP64 masters A64[m] [I_m x Rp] and B64 [Imax x Rp]
+//           that the MU update and the normalisation keep (A and B are then
+//           their FP32 copies, which the Phi family reads)
 //   scratch: carry T [2 x ntiles x Rp] (per-tile partial rows), reductions.
 // Rp is R rounded up so that one factor row is a whole number of 16-byte
 // vectors; the padding columns are zero everywhere and never leave the library.
@@ -84,6 +87,13 @@ struct cpapr_ctx {
     size_t factor_bytes = 0;
     cudaAccessPolicyWindow l2win{};  // persisting-L2 window over factor_block (num_bytes 0: none)
     void *B = nullptr;
+    // FP32 form: FP64 masters of the factors and of B.  The multiplicative
+    // update, the shift S and the normalisation run on them in FP64 and
+    // refresh the FP32 copies A[m] and B that Phi gathers, so an entry that
+    // decays below the FP32 range keeps its FP64 value instead of becoming a
+    // zero that MU could never move again.  Null in the FP64 form.
+    double *A64[CPAPR_MAX_MODES] = {};
+    double *B64 = nullptr;
     void *outbuf = nullptr;  // Phi / MTTKRP output of the one-off calls (Imax x Rp)
     void *Phi[CPAPR_MAX_MODES] = {};
     double *stage = nullptr;  // FP64 staging for I/O (Imax x Rp)
@@ -206,6 +216,8 @@ cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB);     // B = A^(n)
 cpapr_status launch_ll_total(cpapr_ctx *ctx, const double *llpart, int nll, double *dst);
 cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed);
 cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst);   // R cols -> Rp cols, to T
+// factor m from the caller's rows x R doubles (and its FP64 master in the FP32 form)
+cpapr_status upload_factor(cpapr_ctx *ctx, int m, const double *src);
 cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, double *dst); // Rp cols T -> R cols
 cpapr_status launch_kkt_rows(cpapr_ctx *ctx, int n, const void *B, const void *Phi, InnerState *inner);
 
@@ -229,11 +241,32 @@ __device__ __forceinline__ float4 vmul(float4 a, float4 b) {
 }
 __device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 
+// FP32 form of B <- B * Phi on the FP64 master: vector e of four B entries
+// (Bm[4e .. 4e+3]) times the FP32 Phi vector p; returns the FP32 copy.
+__device__ __forceinline__ float4 master_mul(double *__restrict__ Bm, float4 p, int64_t e) {
+    double2 *b = reinterpret_cast<double2 *>(Bm) + 2 * e;
+    double2 lo = b[0], hi = b[1];
+    lo.x *= (double)p.x;
+    lo.y *= (double)p.y;
+    hi.x *= (double)p.z;
+    hi.y *= (double)p.w;
+    b[0] = lo;
+    b[1] = hi;
+    return make_float4((float)lo.x, (float)lo.y, (float)hi.x, (float)hi.y);
+}
+// (never called: the FP64 form has no master)
+__device__ __forceinline__ double2 master_mul(double *__restrict__, double2 p, int64_t) { return p; }
+
 __device__ __forceinline__ unsigned long long ordered_bits(double v) {
     // v >= 0: IEEE bit patterns of non-negative doubles order like the values
     return (unsigned long long)__double_as_longlong(v);
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// FP64 factor m: the master in the FP32 form, the factor itself in FP64
+inline const double *factor64(const cpapr_ctx *ctx, int m) {
+    return ctx->A64[m] ? ctx->A64[m] : reinterpret_cast<const double *>(ctx->esize == 8 ? ctx->A[m] : nullptr);
+}
 
 }  // namespace cpapr

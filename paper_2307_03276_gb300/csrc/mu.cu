@@ -6,7 +6,9 @@
 //   log-likelihood total               ll_total_kernel (column sums, tile
 //                                      partials and the model total at once)
 // and the model I/O helpers.  All reductions that decide or normalise run in
-// FP64 whatever the working precision.
+// FP64 whatever the working precision.  In the FP32 form the factors and B
+// have FP64 masters (A64, B64): S, the update and the normalisation compute
+// on the masters in FP64 and write FP32 copies for the Phi kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,16 +22,19 @@ static unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 152 * 8) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), cap));
 }
 
+
 // ---------------------------------------------------------------------------
 // B <- (A + S) Lambda.  S(i,r) = kappa when this is not the first outer
 // iteration, A(i,r) < kappa_tol and the previous Phi(i,r) > 1 (Chi and
 // Kolda's shift away from inadmissible zeros).  Also resets the mode's
 // inner-loop state.
 // ---------------------------------------------------------------------------
+// A: the FP64 factor (the master in the FP32 form); Bm: FP64 master of B
+// (FP32 form) or null.
 template <typename T>
-__global__ void sb_kernel(const T *__restrict__ A, const T *__restrict__ phi_prev, const double *__restrict__ lambda,
-                          T *__restrict__ B, int64_t rows, int Rp, int shift, double kappa, double kappa_tol,
-                          InnerState *inner) {
+__global__ void sb_kernel(const double *__restrict__ A, const T *__restrict__ phi_prev,
+                          const double *__restrict__ lambda, double *__restrict__ Bm, T *__restrict__ B, int64_t rows,
+                          int Rp, int shift, double kappa, double kappa_tol, InnerState *inner) {
     if (inner && blockIdx.x == 0 && threadIdx.x == 0) {
         inner->l = 0;
         inner->done = 0;
@@ -43,9 +48,11 @@ __global__ void sb_kernel(const T *__restrict__ A, const T *__restrict__ phi_pre
     const int64_t n = rows * Rp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e & (Rp - 1));  // Rp is a power of two
-        const double a = (double)A[e];
+        const double a = A[e];
         const double s = (shift && a < kappa_tol && (double)phi_prev[e] > 1.0) ? kappa : 0.0;
-        B[e] = (T)((a + s) * lambda[c]);
+        const double b = (a + s) * lambda[c];
+        if (Bm) Bm[e] = b;
+        B[e] = (T)b;
     }
 }
 
@@ -55,11 +62,11 @@ cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner) {
     count_launch(ctx);
     if (ctx->esize == 8)
         sb_kernel<double><<<grid_for(rows * ctx->Rp), 256, 0, ctx->stream>>>(
-            (const double *)ctx->A[n], (const double *)ctx->Phi[n], ctx->lambda, (double *)ctx->B, rows, ctx->Rp,
+            factor64(ctx, n), (const double *)ctx->Phi[n], ctx->lambda, nullptr, (double *)ctx->B, rows, ctx->Rp,
             shift ? 1 : 0, ctx->opt.kappa, ctx->opt.kappa_tol, inner);
     else
         sb_kernel<float><<<grid_for(rows * ctx->Rp), 256, 0, ctx->stream>>>(
-            (const float *)ctx->A[n], (const float *)ctx->Phi[n], ctx->lambda, (float *)ctx->B, rows, ctx->Rp,
+            factor64(ctx, n), (const float *)ctx->Phi[n], ctx->lambda, ctx->B64, (float *)ctx->B, rows, ctx->Rp,
             shift ? 1 : 0, ctx->opt.kappa, ctx->opt.kappa_tol, inner);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
@@ -71,9 +78,11 @@ cpapr_status launch_sb(cpapr_ctx *ctx, int n, bool shift, InnerState *inner) {
 // the bookkeeping (iteration counter, done flag, next violation slot, and
 // the graph's loop condition).
 // ---------------------------------------------------------------------------
+// B: the working-precision B; Bm: its FP64 master (FP32 form) or null.
 template <typename T>
-__global__ void update_kernel(T *__restrict__ B, const T *__restrict__ P, int64_t n, InnerState *inner, double tol,
-                              int max_inner, cudaGraphConditionalHandle cond, int use_cond) {
+__global__ void update_kernel(T *__restrict__ B, double *__restrict__ Bm, const T *__restrict__ P, int64_t n,
+                              InnerState *inner, double tol, int max_inner, cudaGraphConditionalHandle cond,
+                              int use_cond) {
     __shared__ int s_l, s_done;
     __shared__ double s_viol;
     if (threadIdx.x == 0) {
@@ -90,8 +99,15 @@ __global__ void update_kernel(T *__restrict__ B, const T *__restrict__ P, int64_
         V *Bv = reinterpret_cast<V *>(B);
         const V *Pv = reinterpret_cast<const V *>(P);
         const int64_t nv = n / Vec16<T>::n;
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv; e += (int64_t)gridDim.x * blockDim.x)
-            Bv[e] = vmul(Bv[e], Pv[e]);
+        if (Bm) {
+            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv;
+                 e += (int64_t)gridDim.x * blockDim.x)
+                Bv[e] = master_mul(Bm, Pv[e], e);
+        } else {
+            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv;
+                 e += (int64_t)gridDim.x * blockDim.x)
+                Bv[e] = vmul(Bv[e], Pv[e]);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -124,12 +140,13 @@ cpapr_status launch_update(cpapr_ctx *ctx, int n, double tol, int max_inner, Inn
     count_launch(ctx);
     const unsigned g = grid_for(nel, 256, 152 * 4);
     if (ctx->esize == 8)
-        update_kernel<double><<<g, 256, 0, ctx->stream>>>((double *)ctx->B, (const double *)ctx->Phi[n], nel, inner,
-                                                           tol, max_inner, (cudaGraphConditionalHandle)cond_handle,
-                                                           use_cond);
+        update_kernel<double><<<g, 256, 0, ctx->stream>>>((double *)ctx->B, nullptr, (const double *)ctx->Phi[n], nel,
+                                                           inner, tol, max_inner,
+                                                           (cudaGraphConditionalHandle)cond_handle, use_cond);
     else
-        update_kernel<float><<<g, 256, 0, ctx->stream>>>((float *)ctx->B, (const float *)ctx->Phi[n], nel, inner, tol,
-                                                          max_inner, (cudaGraphConditionalHandle)cond_handle, use_cond);
+        update_kernel<float><<<g, 256, 0, ctx->stream>>>((float *)ctx->B, ctx->B64, (const float *)ctx->Phi[n], nel,
+                                                          inner, tol, max_inner,
+                                                          (cudaGraphConditionalHandle)cond_handle, use_cond);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
 }
@@ -182,9 +199,11 @@ static int colsum_parts(int64_t rows, int Rp) {
 
 // A(i,c) = B(i,c) / lambda_c (lambda = the column sums of B, finished by
 // colsum_partial_kernel), or A kept when lambda_c = 0 (an all-zero column).
+// B is the FP64 B (the master in the FP32 form); Am is the FP64 master of A
+// (FP32 form; A is then its FP32 copy) or null.
 template <typename T>
-__global__ void normalise_kernel(const T *__restrict__ B, T *__restrict__ A, int64_t rows, int Rp,
-                                 const double *__restrict__ lambda) {
+__global__ void normalise_kernel(const double *__restrict__ B, T *__restrict__ A, double *__restrict__ Am,
+                                 int64_t rows, int Rp, const double *__restrict__ lambda) {
     // one reciprocal per column (no overflow: lambda >= 2^-1000, else a plain
     // division); lambda = 0 marks an all-zero column, whose A stays
     __shared__ double lam[256], inv[256];
@@ -198,7 +217,11 @@ __global__ void normalise_kernel(const T *__restrict__ B, T *__restrict__ A, int
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e & (Rp - 1));  // Rp is a power of two
         const double l = lam[c];
-        if (l > 0.0) A[e] = (T)(inv[c] != 0.0 ? (double)B[e] * inv[c] : (double)B[e] / l);
+        if (l > 0.0) {
+            const double v = inv[c] != 0.0 ? B[e] * inv[c] : B[e] / l;
+            if (Am) Am[e] = v;
+            A[e] = (T)v;
+        }
     }
 }
 
@@ -211,17 +234,16 @@ cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
     ProfScope ps(ctx, K_NORM);
     count_launch(ctx, 2);
     // llcount[1]: the column-sum counter (llcount[0] belongs to the log-likelihood total)
-    if (ctx->esize == 8) {
-        colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>((const double *)ctx->B, rows, Rp, ctx->colpart,
-                                                                      ctx->llcount + 1, ctx->lambda);
-        normalise_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-            (const double *)ctx->B, (double *)ctx->A[n], rows, Rp, ctx->lambda);
-    } else {
-        colsum_partial_kernel<float><<<parts, 256, 0, ctx->stream>>>((const float *)ctx->B, rows, Rp, ctx->colpart,
-                                                                     ctx->llcount + 1, ctx->lambda);
-        normalise_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-            (const float *)ctx->B, (float *)ctx->A[n], rows, Rp, ctx->lambda);
-    }
+    // the column sums and the division run on the FP64 B (the master in the FP32 form)
+    const double *B64 = ctx->B64 ? ctx->B64 : (const double *)ctx->B;
+    colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>(B64, rows, Rp, ctx->colpart, ctx->llcount + 1,
+                                                                  ctx->lambda);
+    if (ctx->esize == 8)
+        normalise_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(B64, (double *)ctx->A[n], nullptr,
+                                                                               rows, Rp, ctx->lambda);
+    else
+        normalise_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(B64, (float *)ctx->A[n], ctx->A64[n],
+                                                                              rows, Rp, ctx->lambda);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
 }
@@ -229,22 +251,27 @@ cpapr_status launch_normalise(cpapr_ctx *ctx, int n) {
 // ---------------------------------------------------------------------------
 // B = A^(n) diag(lambda)
 // ---------------------------------------------------------------------------
+// A: the FP64 factor (the master in the FP32 form); Bm: FP64 master of B or null
 template <typename T>
-__global__ void scale_b_kernel(const T *__restrict__ A, const double *__restrict__ lambda, T *__restrict__ B,
-                               int64_t n, int Rp) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        B[e] = (T)((double)A[e] * lambda[e & (Rp - 1)]);  // Rp is a power of two
+__global__ void scale_b_kernel(const double *__restrict__ A, const double *__restrict__ lambda,
+                               double *__restrict__ Bm, T *__restrict__ B, int64_t n, int Rp) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double b = A[e] * lambda[e & (Rp - 1)];  // Rp is a power of two
+        if (Bm) Bm[e] = b;
+        B[e] = (T)b;
+    }
 }
 
 cpapr_status launch_scale_b(cpapr_ctx *ctx, int n, void *dstB) {
     count_launch(ctx);
     const int64_t nel = ctx->dims[n] * ctx->Rp;
+    // the FP32 form refreshes B's master only when dstB is the context's B
     if (ctx->esize == 8)
-        scale_b_kernel<double><<<grid_for(nel), 256, 0, ctx->stream>>>((const double *)ctx->A[n], ctx->lambda,
+        scale_b_kernel<double><<<grid_for(nel), 256, 0, ctx->stream>>>(factor64(ctx, n), ctx->lambda, nullptr,
                                                                        (double *)dstB, nel, ctx->Rp);
     else
-        scale_b_kernel<float><<<grid_for(nel), 256, 0, ctx->stream>>>((const float *)ctx->A[n], ctx->lambda,
-                                                                      (float *)dstB, nel, ctx->Rp);
+        scale_b_kernel<float><<<grid_for(nel), 256, 0, ctx->stream>>>(
+            factor64(ctx, n), ctx->lambda, dstB == ctx->B ? ctx->B64 : nullptr, (float *)dstB, nel, ctx->Rp);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
 }
@@ -261,7 +288,7 @@ LLTotalArgs ll_total_args(const cpapr_ctx *ctx, const double *llpart, int nll, d
     LLTotalArgs a{};
     int blocks = 0;
     for (int m = 0; m < ctx->N; ++m) {
-        a.A[m] = ctx->A[m];
+        a.A[m] = factor64(ctx, m);  // the column sums run on the FP64 factors
         a.rows[m] = ctx->dims[m];
         a.part0[m] = blocks;
         blocks += colsum_parts(ctx->dims[m], ctx->Rp);
@@ -281,10 +308,7 @@ LLTotalArgs ll_total_args(const cpapr_ctx *ctx, const double *llpart, int nll, d
 cpapr_status launch_ll_total(cpapr_ctx *ctx, const double *llpart, int nll, double *dst) {
     const LLTotalArgs a = ll_total_args(ctx, llpart, nll, dst);
     const int blocks = a.part0[ctx->N];
-    if (ctx->esize == 8)
-        ll_total_kernel<double><<<blocks, 256, 0, ctx->stream>>>(a);
-    else
-        ll_total_kernel<float><<<blocks, 256, 0, ctx->stream>>>(a);
+    ll_total_kernel<double><<<blocks, 256, 0, ctx->stream>>>(a);
     count_launch(ctx);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
@@ -313,10 +337,12 @@ __global__ void rand_fill_kernel(double *__restrict__ dst, int64_t rows, int R, 
     }
 }
 
-// A = stage / colsum (columns with a zero sum stay as they are); lambda *= colsum
+// A = stage / colsum (columns with a zero sum stay as they are); lambda *= colsum.
+// Am: FP64 master of A (FP32 form) or null.
 template <typename T>
-__global__ void init_scale_kernel(const double *__restrict__ stage, T *__restrict__ A, int64_t rows, int Rp,
-                                  const double *__restrict__ part, int nparts, double *__restrict__ lambda) {
+__global__ void init_scale_kernel(const double *__restrict__ stage, T *__restrict__ A, double *__restrict__ Am,
+                                  int64_t rows, int Rp, const double *__restrict__ part, int nparts,
+                                  double *__restrict__ lambda) {
     __shared__ double cs[256];
     for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
         double s = 0.0;
@@ -329,7 +355,9 @@ __global__ void init_scale_kernel(const double *__restrict__ stage, T *__restric
     const int64_t n = rows * Rp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const double s = cs[e % Rp];
-        A[e] = (T)(s > 0.0 ? stage[e] / s : stage[e]);
+        const double v = s > 0.0 ? stage[e] / s : stage[e];
+        if (Am) Am[e] = v;
+        A[e] = (T)v;
     }
 }
 
@@ -350,10 +378,10 @@ cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed) {
         colsum_partial_kernel<double><<<parts, 256, 0, ctx->stream>>>(ctx->stage, rows, Rp, ctx->colpart);
         if (ctx->esize == 8)
             init_scale_kernel<double><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-                ctx->stage, (double *)ctx->A[m], rows, Rp, ctx->colpart, parts, ctx->lambda);
+                ctx->stage, (double *)ctx->A[m], nullptr, rows, Rp, ctx->colpart, parts, ctx->lambda);
         else
             init_scale_kernel<float><<<grid_for(rows * Rp), 256, 0, ctx->stream>>>(
-                ctx->stage, (float *)ctx->A[m], rows, Rp, ctx->colpart, parts, ctx->lambda);
+                ctx->stage, (float *)ctx->A[m], ctx->A64[m], rows, Rp, ctx->colpart, parts, ctx->lambda);
         CPAPR_CUDA(ctx, cudaGetLastError());
     }
     return CPAPR_OK;
@@ -363,12 +391,14 @@ cpapr_status launch_init_random(cpapr_ctx *ctx, uint64_t seed) {
 // model I/O: caller matrices are rows x R doubles (host or device); the
 // device keeps rows x Rp of the working type with zero padding columns.
 // ---------------------------------------------------------------------------
+// dst64: an FP64 copy to write as well (a factor's master in the FP32 form) or null
 template <typename T>
 __global__ void convert_kernel(const double *__restrict__ src, T *__restrict__ dst, int64_t n,
-                               int32_t *__restrict__ errflag) {
+                               int32_t *__restrict__ errflag, double *__restrict__ dst64) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const double v = src[e];
         if (!(v >= 0.0) || isinf(v)) atomicOr(errflag + 2, 1);
+        if (dst64) dst64[e] = v;
         dst[e] = (T)v;
     }
 }
@@ -379,7 +409,7 @@ __global__ void widen_kernel(const T *__restrict__ src, double *__restrict__ dst
         dst[e] = (double)src[e];
 }
 
-cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst) {
+static cpapr_status upload_matrix2(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst, double *dst64) {
     const int R = ctx->R, Rp = ctx->Rp;
     const int64_t n = rows * Rp;
     CPAPR_CUDA(ctx, cudaMemsetAsync(ctx->stage, 0, (size_t)n * 8, ctx->stream));
@@ -388,11 +418,21 @@ cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void
                                           cudaMemcpyDefault, ctx->stream));
     count_launch(ctx);
     if (ctx->esize == 8)
-        convert_kernel<double><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (double *)dst, n, ctx->errflag);
+        convert_kernel<double><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (double *)dst, n, ctx->errflag,
+                                                                     nullptr);
     else
-        convert_kernel<float><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (float *)dst, n, ctx->errflag);
+        convert_kernel<float><<<grid_for(n), 256, 0, ctx->stream>>>(ctx->stage, (float *)dst, n, ctx->errflag,
+                                                                    dst64);
     CPAPR_CUDA(ctx, cudaGetLastError());
     return CPAPR_OK;
+}
+
+cpapr_status upload_matrix(cpapr_ctx *ctx, const double *src, int64_t rows, void *dst) {
+    return upload_matrix2(ctx, src, rows, dst, nullptr);
+}
+
+cpapr_status upload_factor(cpapr_ctx *ctx, int m, const double *src) {
+    return upload_matrix2(ctx, src, ctx->dims[m], ctx->A[m], ctx->A64[m]);
 }
 
 cpapr_status download_matrix(cpapr_ctx *ctx, const void *src, int64_t rows, double *dst) {

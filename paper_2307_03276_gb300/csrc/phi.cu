@@ -87,8 +87,10 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
         if (m == n) continue;
         a.idx[k] = L.idx[k];
         a.A[k] = ctx->A[m];
+        a.Am[k] = ctx->A64[m];
         ++k;
     }
+    a.Bm = ctx->B64;
     a.val = L.val;
     a.B = B;
     a.out = out;

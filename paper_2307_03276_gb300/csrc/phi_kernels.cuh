@@ -76,6 +76,10 @@ struct PhiArgs {
     const void *pi;     // materialised Khatri-Rao rows [nnz][Rp] in mode-n order, or null
     uint32_t stage_extra;  // bytes the staging barrier expects beyond the copies: 0, or 16
                            // when the host injects a staging-wait failure (tests)
+    // FP32 form: FP64 masters of B and of the gathered factors, which the
+    // log-likelihood reads where an FP32 model value underflows (else null)
+    const double *Bm;
+    const double *Am[kMaxNm1];
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -432,18 +436,20 @@ __device__ __forceinline__ void lds_u(const double *p, double (&d)[U]) {
     }
 }
 
-// <B[row], pi> recomputed in FP64 from the stored factor values: the FP32
-// log-likelihood uses it where the FP32 product underflows (m < 2^-96).
+// <B[row], pi> recomputed in FP64 from the FP64 masters of B and of the
+// factors: the FP32 log-likelihood uses it where the FP32 product underflows
+// (m < 2^-96), so the value is the FP64 model's even where FP32 copies of
+// factor entries are zero.
 template <typename T, int RPL, int MAXK>
 __device__ __forceinline__ double dot_fp64(const PhiArgs &a, const int32_t (&ii)[MAXK], int32_t row, int col0, int nm1) {
-    const T *Bm = reinterpret_cast<const T *>(a.B) + (int64_t)row * a.Rp + col0;
+    const double *Bm = a.Bm + (int64_t)row * a.Rp + col0;
     double d = 0.0;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
-        double p = (double)__ldg(Bm + r);
+        double p = __ldg(Bm + r);
 #pragma unroll
         for (int k = 0; k < MAXK; ++k)
-            if (k < nm1) p *= (double)__ldg(reinterpret_cast<const T *>(a.A[k]) + (int64_t)ii[k] * a.Rp + col0 + r);
+            if (k < nm1) p *= __ldg(a.Am[k] + (int64_t)ii[k] * a.Rp + col0 + r);
         d += p;
     }
     return d;

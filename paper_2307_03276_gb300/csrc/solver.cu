@@ -244,7 +244,7 @@ cpapr_status autotune(cpapr_ctx *ctx) {
     CPAPR_CUDA(ctx, cudaEventCreate(&e1));
     // a neutral model for timing: uniform factors
     std::vector<double> ones((size_t)ctx->Imax * ctx->R, 1.0 / 64.0);
-    for (int m = 0; m < ctx->N; ++m) CPAPR_TRY(upload_matrix(ctx, ones.data(), ctx->dims[m], ctx->A[m]));
+    for (int m = 0; m < ctx->N; ++m) CPAPR_TRY(upload_factor(ctx, m, ones.data()));
     std::vector<double> lam(Rp, 1.0);
     CPAPR_CUDA(ctx, cudaMemcpyAsync(ctx->lambda, lam.data(), Rp * 8, cudaMemcpyHostToDevice, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
