@@ -59,15 +59,31 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_GATHER_GBS = 7450.0
 
 
-# DRAM bytes per Phi launch by mode (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# (--set full, the second pass of bench.py --kernel-only) of the kernel configuration named in the key
-# (workload, dtype, Pi form, lanes per mode, tile per mode); a run in any other configuration reports
-# traffic null, and an entry is dropped when its kernel changes.
+# DRAM bytes per Phi launch by mode (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of
+# the kernel configuration named in the key (workload, dtype, Pi form, lanes per mode, tile per mode).
+# "nnz" is the nonzero count of the captured tensor: the 4-way workload was captured on a copy with the
+# same dims, rank and distributions but 1e7 nonzeros (a few GB on the device, as the capture rules ask);
+# its traffic is scaled to the full tensor per mode as (bytes - io) * nnz_full / nnz + io, where io is
+# the algorithmic B read plus Phi write (2 R b_f I_n), the only part that does not grow with the
+# nonzeros.  A run in any other configuration reports traffic null; an entry is dropped when its kernel
+# changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        ([2.8338e9, 2.8274e9, 2.7655e9], "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"),
+        {"bytes": [2.8338e9, 2.8274e9, 2.7655e9], "nnz": 10_000_000,
+         "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
-        ([202.1e6, 201.0e6, 197.4e6], "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"),
+        {"bytes": [202.1e6, 201.0e6, 197.4e6], "nnz": 10_000_000,
+         "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
+    ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
+        {"bytes": [1424822784 + 13699072, 1424786944 + 11576576, 1401487616 + 978944, 1400192000 + 288000],
+         "nnz": 10_000_000,
+         "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
+                   "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
+    ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f32", "materialised", (4, 4, 4, 4), (4096, 4096, 4096, 4096)):
+        {"bytes": [732876288 + 4610304, 732956928 + 2127616, 720758528 + 178432, 720126720 + 218624],
+         "nnz": 10_000_000,
+         "source": "ncu capture of the FP32 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
+                   "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
 }
 
 
@@ -464,25 +480,34 @@ def run_time_to_kkt(args):
     print(json.dumps({"probe": "time_to_kkt", **r}), flush=True)
 
 
-def batched_run(cp, torch, precision, steps, warmup, count=64):
+def batched_run(cp, torch, precision, steps, warmup, count=64, tuned=True):
     """64 uneven 3-way tensors (dims log-uniform up to 20000 x 20000 x 500, nnz
     log-uniform 1e3..1e6, R in {8, 16, 32}): one outer iteration per step for
     the whole batch through the persistent batched solver, and the same work
-    as one cpapr_mu_solve per tensor."""
+    as one cpapr_mu_solve per tensor.  With `tuned`, also the batched step
+    with contexts whose tiles (and FP64 Pi forms) the autotuner chose per
+    shape class through a cache file (tuning time reported apart)."""
     from paper_2307_03276_gb300 import synth
     specs = synth.batch_specs(count=count)
     tensors = [synth.generate(s) for s in specs]
     stream = torch.cuda.current_stream()
     out = {"workload": f"c4_batch{count}_3way", "tensors": count, "nnz_total": int(sum(T.nnz for T in tensors)),
            "ranks": sorted({int(T.rank) for T in tensors})}
-    for mode in ("batched", "per_tensor"):
-        ts = [cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, stream=stream.cuda_stream)
+    cache_dir = tempfile.mkdtemp(prefix="cpapr_tune_")
+    modes = ("batched", "per_tensor", "batched_tuned") if tuned else ("batched", "per_tensor")
+    for mode in modes:
+        extra = {}
+        t0 = time.perf_counter()
+        if mode == "batched_tuned":
+            extra = {"autotune": 1, "tune_cache": os.path.join(cache_dir, "tune.txt")}
+        ts = [cp.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, stream=stream.cuda_stream, **extra)
               for T in tensors]
+        create_s = time.perf_counter() - t0
         for T, t in zip(tensors, ts):
             t.set_model(np.ones(T.rank), synth.random_factors(T.dims, T.rank, T.seed + 3))
 
         def step():
-            if mode == "batched":
+            if mode != "per_tensor":
                 res = cp.cpapr_batch_mu_solve([t.ctx for t in ts], TOL, 1, MAX_INNER)
             else:
                 res = [t.mu_solve(TOL, 1, MAX_INNER) for t in ts]
@@ -501,9 +526,16 @@ def batched_run(cp, torch, precision, steps, warmup, count=64):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         out[mode] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps}
+        if mode == "batched_tuned":
+            out[mode]["create_with_tuning_s"] = create_s
+            with open(extra["tune_cache"]) as f:
+                out[mode]["shape_classes_tuned"] = len(f.read().splitlines())
+            out[mode]["tiles_mode0"] = sorted({int(t.info().tile_nnz[0]) for t in ts})
         for t in ts:
             t.close()
     out["speedup_vs_per_tensor"] = out["batched"]["value"] / out["per_tensor"]["value"]
+    if tuned:
+        out["tuned_vs_heuristic"] = out["batched_tuned"]["value"] / out["batched"]["value"]
     return out
 
 
@@ -516,16 +548,22 @@ def kernel_breakdown(stats, steps):
 
 
 def ncu_traffic(T, dtype, mat, info, inner_per_mode):
-    """Measured DRAM bytes per Phi launch for this configuration, weighted by
-    the launches of each mode, with its source; (None, None) if not captured."""
+    """Measured DRAM bytes per Phi launch for this configuration (scaled to the
+    tensor's nonzeros where the capture ran on a smaller copy), weighted by the
+    launches of each mode, with its source; (None, None) if not captured."""
     N = T.nmodes
     form = "materialised" if all(mat) else ("fused" if not any(mat) else "mixed")
     key = (T.name, dtype, form, tuple(info.rank_lanes)[:N], tuple(info.tile_nnz)[:N])
     if key not in NCU_TRAFFIC:
         return None, None
-    per_mode, src = NCU_TRAFFIC[key]
+    ent = NCU_TRAFFIC[key]
+    fb = 8 if dtype == "f64" else 4
+    per_mode = []
+    for n in range(N):
+        io = 2.0 * T.rank * fb * T.dims[n]
+        per_mode.append((ent["bytes"][n] - io) * T.nnz / ent["nnz"] + io)
     w = [float(inner_per_mode[n]) for n in range(N)]
-    return sum(w[n] * per_mode[n] for n in range(N)) / max(sum(w), 1.0), src
+    return sum(w[n] * per_mode[n] for n in range(N)) / max(sum(w), 1.0), ent["source"]
 
 
 def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, info=None):

@@ -79,7 +79,22 @@ enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
  *             early exit (default), 0 = plain stream launches.
  *  autotune   1 = time candidate (tile_nnz, rank_lanes, reduction, pi_mode)
  *             choices on the tensor when it is created and keep the fastest
- *             per mode; 0 = use the built-in heuristic (default).
+ *             per mode; 0 = use the built-in heuristic (default).  Each
+ *             candidate is timed as a Phi of the MU inner loop runs (with
+ *             its KKT reduction, and for atomic adds the zeroing and the
+ *             separate KKT pass they need).  Timing replaces the model; set
+ *             one after cpapr_create.
+ *  tune_cache NULL (default) or the path of a text file of tuned choices,
+ *             one line per shape class: precision, number of modes, padded
+ *             rank, and power-of-two buckets of the nonzeros, of the mode's
+ *             rows and of the nonzeros per non-empty row.  At create each
+ *             mode whose class is in the file takes the cached choice (no
+ *             timing); with autotune = 1 the other modes are timed and their
+ *             choices appended to the file, with autotune = 0 they keep the
+ *             heuristic.  Lines that do not parse, or choices that do not
+ *             fit this tensor, are ignored.  cpapr_batch_mu_solve keeps each
+ *             context's tile size and Pi form (its lanes and reduction are
+ *             fixed by the batched kernel).
  *  profile    1 = record CUDA events around every Phi launch so that
  *             cpapr_kernel_stats() can report per-kernel device time.
  *  pi_mode    the Khatri-Rao rows Pi of Algorithm 3.  CPAPR_PI_FUSED: formed
@@ -119,7 +134,8 @@ typedef struct {
     int32_t profile;
     int32_t pi_mode;
     int32_t l2_persist;
-    int32_t reserved[3];
+    int32_t reserved;
+    const char *tune_cache;
 } cpapr_options;
 
 void cpapr_default_options(cpapr_options *opt);

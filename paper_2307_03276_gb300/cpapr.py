@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("kappa_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile_nnz", ctypes.c_int32), ("rank_lanes", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("pi_mode", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("pi_mode", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class Result(ctypes.Structure):
@@ -151,6 +152,8 @@ def cpapr_default_options(**overrides) -> Options:
     for k, v in overrides.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
+        if k == "tune_cache" and v is not None and not isinstance(v, bytes):
+            v = os.fsencode(v)
         setattr(o, k, v)
     return o
 

@@ -498,7 +498,8 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
         CR_TRY(configure_mode(ctx, n, lanes, tile, red));
         CR_TRY(configure_pi(ctx, n, pi));
     }
-    if (o.autotune) CR_TRY(autotune(ctx));
+    if (o.autotune || o.tune_cache) CR_TRY(autotune(ctx));
+    ctx->opt.tune_cache = nullptr;  // the caller's string is not kept
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build"));
 #undef CR_TRY

@@ -584,15 +584,25 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
         ctxs[i]->pi_mode_built = -1;  // the batched solve changes every factor
     }
-    // every tensor needs a rank class of the batched kernel and the segmented reduction
+    // every tensor needs a rank class of the batched kernel and the segmented
+    // reduction; it keeps its own tile size (tuned or heuristic) as long as
+    // the stage leaves the batched kernel its resident blocks per SM (the
+    // whole launch runs at the largest tile's shared memory), else the tile
+    // is halved until it does
+    int maxrpl = 0;
+    for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
+    const size_t budget = (size_t)227 * 1024 / batch_min_blocks<T>() - 1024;
     for (int i = 0; i < count; ++i) {
         const int k = class_for<T>(ctxs[i]->Rp);
         if (k < 0) return fail(ctxs[i], CPAPR_E_ARG, "rank not supported by the batched solver");
-        const int lanes = (sizeof(T) == 8 ? Classes<T>::g[k] : Classes<T>::g[k]);
+        const int lanes = Classes<T>::g[k];
         for (int n = 0; n < N; ++n) {
             ModeLayout &L = ctxs[i]->mode[n];
-            if (L.lanes != lanes || L.reduction != CPAPR_REDUCE_SEGMENTED)
-                CPAPR_TRY(configure_mode(ctxs[i], n, lanes, L.tile_nnz, CPAPR_REDUCE_SEGMENTED));
+            int tile = L.tile_nnz;
+            while (tile > 256 && phi_smem_bytes(tile, N - 1, (int)sizeof(T), batch_threads<T>(), maxrpl) > budget)
+                tile /= 2;
+            if (L.lanes != lanes || L.reduction != CPAPR_REDUCE_SEGMENTED || tile != L.tile_nnz)
+                CPAPR_TRY(configure_mode(ctxs[i], n, lanes, tile, CPAPR_REDUCE_SEGMENTED));
         }
         CPAPR_CUDA(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
     }
@@ -724,8 +734,7 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
         });
         mp.ntiles = (int)tiles.size();
         {
-            int maxrpl = 0, maxtile = 4;
-            for (int k = 0; k < Classes<T>::n; ++k) maxrpl = std::max(maxrpl, Classes<T>::rpl[k]);
+            int maxtile = 4;
             for (int i = 0; i < count; ++i) maxtile = std::max(maxtile, ctxs[i]->mode[n].tile_nnz);
             mp.smem = phi_smem_bytes(maxtile, N - 1, (int)sizeof(T), batch_threads<T>(), maxrpl);
             smem_max = std::max(smem_max, mp.smem);

@@ -326,6 +326,10 @@ __device__ __forceinline__ void store_row(T *__restrict__ base, const T (&src)[R
 // failure in *a.err, waits once more for its copies and skips the tile (the
 // host then reports CPAPR_E_TIMEOUT).
 
+// The limit is a hang guard, not a performance bound: a tile's copies land in
+// microseconds, so only a copy that can never complete (or a GPU so starved
+// that one tile's few kilobytes take a second) reaches it, and then the call
+// reports CPAPR_E_TIMEOUT instead of hanging the GPU.
 constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s
 
 // entries reserved per staged stream (a multiple of 4: 16-byte rows)

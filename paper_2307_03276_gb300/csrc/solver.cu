@@ -18,6 +18,10 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -231,14 +235,94 @@ cpapr_status batch_mu_solve(cpapr_ctx *const *ctxs, int count, double tol, int m
     return CPAPR_OK;
 }
 
-// Times each supported (lanes, tile, reduction) choice on the tensor's own
-// data, one Phi per candidate after a warm-up, and keeps the fastest per
-// mode -- the analogue of the paper's Kokkos policy grid search
+// ---- tuned-choice cache -------------------------------------------------------
+// One text line per shape class:
+//   cpapr-tune-1 <key> <lanes> <tile> <reduction> <pi> <ms>
+// The key names what the best choice depends on: the precision, the number
+// of modes, the padded rank and power-of-two buckets of the nonzeros, of the
+// mode's rows and of the nonzeros per non-empty row (how many rows a tile
+// crosses).  The last line of a key wins.
+struct TuneChoice {
+    int lanes = 0, tile = 0, reduction = 0, pi = 0;
+};
+
+static int log2_bucket(double v) { return v >= 1.0 ? (int)std::lround(std::log2(v)) : 0; }
+
+static std::string tune_key(const cpapr_ctx *ctx, int n) {
+    const ModeLayout &L = ctx->mode[n];
+    const double rows = (double)ctx->dims[n];
+    const double nonempty = std::max(1.0, rows - (double)L.nempty);
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%s/N%d/Rp%d/nnz2^%d/rows2^%d/per_row2^%d", ctx->esize == 8 ? "f64" : "f32", ctx->N,
+                  ctx->Rp, log2_bucket((double)ctx->nnz), log2_bucket(rows), log2_bucket((double)ctx->nnz / nonempty));
+    return buf;
+}
+
+static std::mutex g_tune_mu;
+
+static bool tune_lookup(const char *path, const std::string &key, TuneChoice *out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512], k[256];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        TuneChoice c;
+        float ms = 0.f;
+        if (std::sscanf(line, "cpapr-tune-1 %255s %d %d %d %d %f", k, &c.lanes, &c.tile, &c.reduction, &c.pi, &ms) == 6 &&
+            key == k) {
+            *out = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void tune_store(const char *path, const std::string &key, const TuneChoice &c, float ms) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;  // an unwritable cache only costs the next create its timing
+    std::fprintf(f, "cpapr-tune-1 %s %d %d %d %d %.6f\n", key.c_str(), c.lanes, c.tile, c.reduction, c.pi, ms);
+    std::fclose(f);
+}
+
+// A cached choice this tensor can run (else it is ignored).
+static bool choice_fits(const cpapr_ctx *ctx, const TuneChoice &c) {
+    if (!phi_config_supported((int)ctx->esize, ctx->N - 1, ctx->Rp, c.lanes)) return false;
+    if (c.tile < 64 || c.tile > (1 << 20) || c.tile % 4) return false;
+    if (c.reduction != CPAPR_REDUCE_ATOMIC && c.reduction != CPAPR_REDUCE_SEGMENTED) return false;
+    if (c.pi != 0 && c.pi != 1) return false;
+    if (c.pi && !pi_fits(ctx)) return false;
+    return phi_smem_for((int)ctx->esize, ctx->N - 1, c.tile, ctx->Rp, c.lanes) <= kMaxPhiSmem;
+}
+
+// Times each supported (lanes, tile, reduction, Pi form) choice on the
+// tensor's own data, one Phi per candidate after a warm-up, and keeps the
+// fastest per mode -- the analogue of the paper's Kokkos policy grid search
 // (league / team / vector sizes, Experiments 3 to 6), chosen per mode
-// because the paper finds the best policy differs across modes.
+// because the paper finds the best policy differs across modes.  Each
+// candidate runs as a Phi of the MU inner loop does: with the mode's inner
+// state, so the segmented form publishes its fused KKT violation and the
+// atomic form pays for zeroing its output and its separate KKT pass.  With a
+// cache file, modes whose shape class it holds take the cached choice.
 cpapr_status autotune(cpapr_ctx *ctx) {
     if (ctx->nnz == 0) return CPAPR_OK;
     const int Rp = ctx->Rp;
+    const char *cache = ctx->opt.tune_cache;
+    std::vector<std::string> keys(ctx->N);
+    std::vector<int> todo;
+    for (int n = 0; n < ctx->N; ++n) {
+        keys[n] = tune_key(ctx, n);
+        TuneChoice c;
+        if (cache && tune_lookup(cache, keys[n], &c) && choice_fits(ctx, c)) {
+            CPAPR_TRY(configure_mode(ctx, n, c.lanes, c.tile, c.reduction));
+            CPAPR_TRY(configure_pi(ctx, n, c.pi));
+        } else if (ctx->opt.autotune) {
+            todo.push_back(n);
+        }
+    }
+    if (todo.empty()) return CPAPR_OK;
     cudaEvent_t e0, e1;
     CPAPR_CUDA(ctx, cudaEventCreate(&e0));
     CPAPR_CUDA(ctx, cudaEventCreate(&e1));
@@ -248,11 +332,15 @@ cpapr_status autotune(cpapr_ctx *ctx) {
     std::vector<double> lam(Rp, 1.0);
     CPAPR_CUDA(ctx, cudaMemcpyAsync(ctx->lambda, lam.data(), Rp * 8, cudaMemcpyHostToDevice, ctx->stream));
     CPAPR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int n = 0; n < ctx->N; ++n) {
+    for (int n : todo) {
         CPAPR_TRY(launch_scale_b(ctx, n, ctx->B));
+        InnerState *inner = ctx->inner + n;
         float best = 1e30f;
-        int bl = ctx->mode[n].lanes, bt = ctx->mode[n].tile_nnz, br = ctx->mode[n].reduction;
-        int bp = ctx->mode[n].pi;
+        TuneChoice bc;
+        bc.lanes = ctx->mode[n].lanes;
+        bc.tile = ctx->mode[n].tile_nnz;
+        bc.reduction = ctx->mode[n].reduction;
+        bc.pi = ctx->mode[n].pi;
         const int tiles[] = {1024, 2048, 4096, 8192};
         // the materialised Khatri-Rao rows are a candidate where their buffer
         // fits (the fixed cost of building them once per inner loop is not
@@ -270,25 +358,29 @@ cpapr_status autotune(cpapr_ctx *ctx) {
                     CPAPR_TRY(configure_mode(ctx, n, lanes, tile, red));
                     CPAPR_TRY(configure_pi(ctx, n, pi));
                     if (pi) CPAPR_TRY(launch_pi_build(ctx, n));
-                    CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, nullptr));
+                    // a fresh inner state: not done, violation slots clear
+                    CPAPR_CUDA(ctx, cudaMemsetAsync(inner, 0, sizeof(InnerState), ctx->stream));
+                    CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, inner));
                     CPAPR_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-                    for (int rep = 0; rep < 3; ++rep) CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, nullptr));
+                    for (int rep = 0; rep < 3; ++rep) CPAPR_TRY(launch_phi(ctx, n, OP_PHI, ctx->B, ctx->outbuf, inner));
                     CPAPR_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
                     CPAPR_CUDA(ctx, cudaEventSynchronize(e1));
                     float ms = 0.f;
                     CPAPR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
                     if (ms < best) {
                         best = ms;
-                        bl = lanes;
-                        bt = tile;
-                        br = red;
-                        bp = pi;
+                        bc.lanes = lanes;
+                        bc.tile = tile;
+                        bc.reduction = red;
+                        bc.pi = pi;
                     }
                 }
             }
         }
-        CPAPR_TRY(configure_mode(ctx, n, bl, bt, br));
-        CPAPR_TRY(configure_pi(ctx, n, bp));
+        CPAPR_TRY(configure_mode(ctx, n, bc.lanes, bc.tile, bc.reduction));
+        CPAPR_TRY(configure_pi(ctx, n, bc.pi));
+        CPAPR_CUDA(ctx, cudaMemsetAsync(inner, 0, sizeof(InnerState), ctx->stream));
+        if (cache) tune_store(cache, keys[n], bc, best / 3.f);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

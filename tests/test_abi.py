@@ -57,13 +57,15 @@ def test_ctypes_structs_match_c_layout(tmp_path):
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(cpapr_options),"
         " offsetof(cpapr_options, stream), offsetof(cpapr_options, profile), sizeof(cpapr_result),"
         " offsetof(cpapr_result, loglik), sizeof(cpapr_info), offsetof(cpapr_info, device_bytes),"
-        " offsetof(cpapr_options, l2_persist), offsetof(cpapr_info, l2_window_bytes));return 0;}\n")
+        " offsetof(cpapr_options, l2_persist), offsetof(cpapr_info, l2_window_bytes));"
+        "printf(\"%zu\\n\", offsetof(cpapr_options, tune_cache));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(cpapr.Options), cpapr.Options.stream.offset, cpapr.Options.profile.offset,
             ctypes.sizeof(cpapr.Result), cpapr.Result.loglik.offset, ctypes.sizeof(cpapr.Info),
-            cpapr.Info.device_bytes.offset, cpapr.Options.l2_persist.offset, cpapr.Info.l2_window_bytes.offset]
+            cpapr.Info.device_bytes.offset, cpapr.Options.l2_persist.offset, cpapr.Info.l2_window_bytes.offset,
+            cpapr.Options.tune_cache.offset]
     assert got == want
 
 

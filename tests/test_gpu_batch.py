@@ -191,3 +191,28 @@ def test_full_64_tensor_batch_equals_individual_solves(precision):
                 got = t.phi(n)[rows]
                 assert _rel(got, want) <= (1e-12 if fp64 else 1e-5), (i, n)
         t.close()
+
+
+@pytest.mark.parametrize("precision", [cpapr.CPAPR_FP64, cpapr.CPAPR_FP32])
+def test_batch_with_tuned_contexts_matches_oracle(tmp_path, precision):
+    """Contexts whose tiles (and, in FP64, Pi forms) come from the tuning
+    cache solve together: the batched solver keeps each context's tile as
+    long as it fits its shared-memory budget, and the result matches the
+    oracle's solve of each tensor."""
+    Ts = batch_tensors(seed=79)
+    ms = models(Ts)
+    path = tmp_path / "tune.txt"
+    batch = [cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, autotune=1, tune_cache=str(path))
+             for T in Ts]
+    assert path.exists() and len(path.read_text().splitlines()) >= 1
+    for t, (lam, fs) in zip(batch, ms):
+        t.set_model(lam, fs)
+    res = cpapr.cpapr_batch_mu_solve([t.ctx for t in batch], 1e-4, 3, 5)
+    fp64 = precision == cpapr.CPAPR_FP64
+    for T, t, (lam, fs), r in zip(Ts, batch, ms, res):
+        lb, fb = t.get_model()
+        ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=3, max_inner=5)
+        assert r["total_inner"] == ref["total_inner"]
+        np.testing.assert_allclose(lb, ref["lambda"], rtol=1e-10 if fp64 else 1e-5)
+        assert abs(r["loglik"] - ref["loglik"][-1]) <= (1e-11 if fp64 else 1e-6) * abs(ref["loglik"][-1])
+        t.close()

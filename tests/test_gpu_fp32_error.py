@@ -6,7 +6,8 @@ log-likelihood sum and the normalisation; the factors and B have FP64
 masters that the multiplicative update and the normalisation keep, so an
 entry that decays below the FP32 range keeps its FP64 value.  This test
 measures the error against the FP64 oracle on the 3-way and 4-way Zipf
-workloads (scaled so the oracle runs in seconds): Phi of every mode on the
+workloads (scaled so the oracle runs in seconds, with the FP64
+log-likelihood finite over the five outer iterations): Phi of every mode on the
 same model, and the model and log-likelihood after five outer iterations of
 Algorithm 1 (up to ten inner iterations each) from the same start.  It prints
 one line per workload and asserts:
@@ -73,7 +74,12 @@ def fp32_trajectory_bound(T, lam, fs, phi_err):
 
 CASES = {
     "3-way": lambda: synth.generate(synth.scaled(synth.C2, 200_000, dims=(20_000, 20_000, 1_000))),
-    "4-way": lambda: synth.generate(synth.scaled(synth.C3, 300_000, dims=(40_000, 40_000, 10_000, 365))),
+    # denser than the full tensor: on sparser 4-way cases (e.g. 40000 x 40000 x
+    # 10000 x 365 with the same nonzeros) the FP64 oracle's own model value of
+    # some nonzero underflows to exactly 0 within three outer iterations (the
+    # epsilon-clamped update keeps shrinking a starved nonzero's rows), so its
+    # log-likelihood is -inf and there is nothing finite to compare
+    "4-way": lambda: synth.generate(synth.scaled(synth.C3, 300_000, dims=(5_000, 5_000, 1_000, 100))),
 }
 
 

@@ -679,3 +679,66 @@ def test_mu_shift_moves_an_inadmissible_zero(precision):
         np.testing.assert_allclose(lg, ref["lambda"], rtol=1e-5)
         for A, Ar in zip(fg, ref["factors"]):
             np.testing.assert_allclose(A, Ar, rtol=1e-4, atol=1e-6 * Ar.max())
+
+
+def _cache_lines(path):
+    out = {}
+    for line in path.read_text().splitlines():
+        f = line.split()
+        assert f[0] == "cpapr-tune-1" and len(f) == 7
+        out[f[1]] = tuple(int(x) for x in f[2:6])  # the last line of a key wins
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(cpapr.CPAPR_FP64, 1e-12), (cpapr.CPAPR_FP32, 1e-5)])
+def test_tune_cache_written_then_reused(tmp_path, precision, tol):
+    """autotune with a cache file times every mode once and appends one line
+    per mode; a second context of the same tensor with autotune off reads the
+    cached (lanes, tile, reduction, Pi form) for every mode without timing,
+    and its Phi matches the oracle."""
+    T = case("c3s")
+    lam, fs = model_for(T, 23)
+    path = tmp_path / "tune.txt"
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, autotune=1, tune_cache=str(path)) as t:
+        first = t.info()
+    lines = path.read_text().splitlines()
+    assert len(lines) == T.nmodes
+    cached = _cache_lines(path)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, tune_cache=str(path)) as t:
+        info = t.info()
+        got = {(info.rank_lanes[n], info.tile_nnz[n], info.reduction[n],
+                int(info.pi_mode[n] == cpapr.CPAPR_PI_MATERIALISED)) for n in range(T.nmodes)}
+        assert got <= set(cached.values())
+        if len(cached) == T.nmodes:  # every mode its own class: the same choices as the timed context
+            for n in range(T.nmodes):
+                assert (info.rank_lanes[n], info.tile_nnz[n], info.reduction[n], info.pi_mode[n]) == (
+                    first.rank_lanes[n], first.tile_nnz[n], first.reduction[n], first.pi_mode[n])
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= tol, n
+    assert path.read_text().splitlines() == lines  # a hit times nothing and writes nothing
+
+
+def test_tune_cache_ignores_lines_that_do_not_fit(tmp_path):
+    """A cache line with a choice this tensor cannot run (a lanes count its
+    rank does not allow, a tile too large for shared memory) or that does not
+    parse is ignored: the context keeps the heuristic and works."""
+    T = case("c2s")
+    lam, fs = model_for(T, 24)
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+        heur = t.info()
+    path = tmp_path / "bad.txt"
+    # learn this tensor's keys by tuning into a scratch file
+    probe = tmp_path / "probe.txt"
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, autotune=1, tune_cache=str(probe)):
+        pass
+    keys = list(_cache_lines(probe))
+    path.write_text("garbage line\n" + "".join(f"cpapr-tune-1 {k} 3 1048576 2 0 1.0\n" for k in keys))
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, tune_cache=str(path)) as t:
+        info = t.info()
+        assert list(info.tile_nnz[:3]) == list(heur.tile_nnz[:3])
+        assert list(info.rank_lanes[:3]) == list(heur.rank_lanes[:3])
+        t.set_model(lam, fs)
+        want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[0] * lam[None, :], 0)
+        assert max_rel(t.phi(0), want) <= 1e-12
