@@ -352,6 +352,7 @@ void cpapr_destroy(cpapr_ctx *ctx) {
     for (int n = 0; n < ctx->N; ++n) {
         ModeLayout &L = ctx->mode[n];
         if (L.row_first) cudaFreeAsync(L.row_first, ctx->stream);
+        if (L.krow) cudaFreeAsync(L.krow, ctx->stream);
         if (L.split) cudaFreeAsync(L.split, ctx->stream);
         if (L.tsplit) cudaFreeAsync(L.tsplit, ctx->stream);
         if (L.splitcnt) cudaFreeAsync(L.splitcnt, ctx->stream);

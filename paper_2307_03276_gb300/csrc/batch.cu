@@ -681,7 +681,9 @@ cpapr_status batch_solve_t(cpapr_ctx *const *ctxs, int count, double tol, int ma
             a.In = L.In;
             a.nm1 = c->N - 1;
             a.atomic = 0;
-            a.rid = L.rid;
+            a.rstart = L.rstart;
+            a.nzrow = L.nzrow;
+            a.krow = L.krow;
             int k = 0;
             for (int m = 0; m < N; ++m) {
                 if (m == n) continue;

@@ -279,6 +279,28 @@ __global__ void empty_write_kernel(const int32_t *__restrict__ seg, int32_t In, 
         if (seg[i] == seg[i + 1]) erows[pos[i]] = (int32_t)i;
 }
 
+// nzrow[k] = the k-th row holding nonzeros (pos: exclusive scan of the
+// empty-row flags, so row i is preceded by pos[i] empty rows)
+__global__ void nzrow_kernel(const int32_t *__restrict__ seg, int32_t In, const uint32_t *__restrict__ pos,
+                             int32_t *__restrict__ nzrow) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < In; i += (int64_t)gridDim.x * blockDim.x)
+        if (seg[i] != seg[i + 1]) nzrow[i - pos[i]] = (int32_t)i;
+}
+
+// Row-start bits of the sorted positions: bit p of word p / 32 is set where
+// a row begins (p = 0 or keys[p] != keys[p - 1]); one warp per word.
+__global__ void rstart_kernel(const uint32_t *__restrict__ keys, int64_t nnz, uint32_t *__restrict__ bits) {
+    const int64_t nwords = (nnz + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwords;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t p = w * 32 + lane;
+        const bool start = p < nnz && (p == 0 || keys[p] != keys[p - 1]);
+        const uint32_t b = __ballot_sync(0xffffffffu, start);
+        if (lane == 0) bits[w] = b;
+    }
+}
+
 __global__ void gather_i32_kernel(const int32_t *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
                                   int32_t *__restrict__ dst) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -385,9 +407,12 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         void *p = nullptr;
         BL_TRY(dev_alloc(ctx, &p, (size_t)(L.In + 1) * 4));
         L.seg = (int32_t *)p;
-        BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
-        L.rid = (int32_t *)p;
-        BL_CUDA(cudaMemsetAsync(L.rid + nnz, 0xff, (size_t)(np - nnz) * 4, s));  // -1: no row past the last nonzero
+        // row-start bits: a word per 32 sorted positions, zero past nnz, with
+        // whole 16-byte groups to spare for the tile kernels' bulk copies
+        const size_t words = ((size_t)(np + 31) / 32 + 8 + 3) & ~(size_t)3;
+        BL_TRY(dev_alloc(ctx, &p, words * 4));
+        L.rstart = (uint32_t *)p;
+        BL_CUDA(cudaMemsetAsync(L.rstart, 0, words * 4, s));
         for (int k = 0; k < N - 1; ++k) {
             BL_TRY(dev_alloc(ctx, &p, (size_t)np * 4));
             L.idx[k] = (int32_t *)p;
@@ -432,7 +457,7 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
                 BL_CUDA(cudaFreeAsync(stage[n], s));
                 stage[n] = nullptr;
             }
-            // sort mode n by its row: sorted row ids (rid), row offsets (seg), the permutation
+            // sort mode n by its row: row offsets (seg), row-start bits, the permutation
             ModeLayout &L = ctx->mode[n];
             BL_CUDA(cudaMemcpyAsync(keys, idx32[n], nnz * 4, cudaMemcpyDeviceToDevice, s));
             iota_kernel<<<grid_for(nnz), 256, 0, s>>>(perm[n], nnz);
@@ -442,8 +467,9 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
             BL_TRY(radix_sort(ctx, keys, perm[n], tk, tv, nnz, bits));
             seg_kernel<<<grid_for(nnz), 256, 0, s>>>(keys, nnz, L.In, L.seg);
             BL_CUDA(cudaGetLastError());
-            BL_CUDA(cudaMemcpyAsync(L.rid, keys, nnz * 4, cudaMemcpyDeviceToDevice, s));
-            count_launch(ctx, 3);  // narrow, iota, seg
+            rstart_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, L.rstart);
+            BL_CUDA(cudaGetLastError());
+            count_launch(ctx, 4);  // narrow, iota, seg, row-start bits
         }
         if (vsrc) {
             copy_check_values_kernel<<<grid_for(nnz), 256, 0, cs>>>(vsrc, nnz, vals, ctx->errflag);
@@ -508,7 +534,14 @@ cpapr_status build_layouts(cpapr_ctx *ctx, const int64_t *const *idx_in, const d
         L.erows = (int32_t *)p;
         empty_write_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flags[n], L.erows);
         BL_CUDA(cudaGetLastError());
-        count_launch(ctx);
+        // the rows with nonzeros, increasing (+ 16-byte groups to spare for bulk copies)
+        L.K = L.In - L.nempty;
+        BL_TRY(dev_alloc(ctx, &p, (size_t)(L.K + 8) * 4));
+        L.nzrow = (int32_t *)p;
+        BL_CUDA(cudaMemsetAsync(L.nzrow, 0, (size_t)(L.K + 8) * 4, s));
+        nzrow_kernel<<<grid_for(L.In), 256, 0, s>>>(L.seg, L.In, flags[n], L.nzrow);
+        BL_CUDA(cudaGetLastError());
+        count_launch(ctx, 2);
     }
     cleanup();
     BL_CUDA(cudaStreamSynchronize(s));
@@ -537,6 +570,28 @@ __global__ void tile_rows_kernel(const int32_t *__restrict__ seg, int32_t In, in
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     row_first[t] = upper_bound_seg(seg, 0, In, (int64_t)t * T) - 1;
+}
+
+// krow[t] = index in nzrow of row_first[t] (nzrow is increasing and holds it);
+// krow[ntiles] = K - 1, the last row
+__global__ void tile_krow_kernel(const int32_t *__restrict__ nzrow, int32_t K, const int32_t *__restrict__ row_first,
+                                 int32_t ntiles, int32_t *__restrict__ krow) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    if (t == ntiles) {
+        krow[t] = K - 1;
+        return;
+    }
+    const int32_t r = row_first[t];
+    int32_t lo = 0, hi = K;  // first k with nzrow[k] >= r
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (nzrow[mid] < r)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    krow[t] = lo;
 }
 
 __global__ void split_flags_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ row_first, int32_t T,
@@ -590,10 +645,11 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     ModeLayout &L = ctx->mode[n];
     cudaStream_t s = ctx->stream;
     if (L.row_first) cudaFreeAsync(L.row_first, s);
+    if (L.krow) cudaFreeAsync(L.krow, s);
     if (L.split) cudaFreeAsync(L.split, s);
     if (L.tsplit) cudaFreeAsync(L.tsplit, s);
     if (L.splitcnt) cudaFreeAsync(L.splitcnt, s);
-    L.row_first = L.split = L.tsplit = L.splitcnt = nullptr;
+    L.row_first = L.krow = L.split = L.tsplit = L.splitcnt = nullptr;
     L.tile_nnz = tile_nnz;
     L.ntiles = (int32_t)ceil_div(ctx->nnz, tile_nnz);
     L.nsplit = 0;
@@ -602,6 +658,12 @@ cpapr_status build_tiles(cpapr_ctx *ctx, int n, int tile_nnz) {
     count_launch(ctx, nt >= 2 ? 3 : 1);
     tile_rows_kernel<<<(unsigned)ceil_div(std::max(nt, 1), 256), 256, 0, s>>>(L.seg, L.In, tile_nnz, nt, L.row_first);
     CPAPR_CUDA(ctx, cudaGetLastError());
+    CPAPR_CUDA(ctx, lib_malloc((void **)&L.krow, (size_t)(nt + 1) * 4, s));
+    if (ctx->nnz > 0) {
+        tile_krow_kernel<<<(unsigned)ceil_div(nt + 1, 256), 256, 0, s>>>(L.nzrow, L.K, L.row_first, nt, L.krow);
+        CPAPR_CUDA(ctx, cudaGetLastError());
+        count_launch(ctx);
+    }
     if (nt >= 2) {
         uint32_t *flag = nullptr, *dtot = nullptr;
         CPAPR_CUDA(ctx, lib_malloc((void **)&flag, (size_t)nt * 4 + 4, s));

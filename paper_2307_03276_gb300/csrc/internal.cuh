@@ -3,12 +3,14 @@
 // Device layout of one context (all allocations owned by the context):
 //   per mode n (sorted by i_n once, at create):
 //     seg[n]      int32 [I_n + 1]    first sorted position of each row
-//     rid[n]      int32 [nnz_pad]    i_n of each nonzero in mode-n order (-1 past nnz)
+//     rstart[n]   uint32 bits        bit p set where a row starts at sorted position p
+//     nzrow[n]    int32 [K_n]        the rows holding nonzeros, increasing (K_n of them)
 //     idx[n][k]   int32 [nnz_pad]    coordinate of the k-th other mode (k = 0..N-2,
 //                                    increasing mode number), in mode-n order
 //     val[n]      T     [nnz_pad]    counts in mode-n order (T = double or float)
-//     tile table  row_first[t], the rows that span tiles, each tile's
-//                 split of its head and tail partial, per-split counters
+//     tile table  row_first[t], krow[t] (index in nzrow of the row holding
+//                 the tile's first nonzero), the rows that span tiles, each
+//                 tile's split of its head and tail partial, per-split counters
 //   model:  A[m] T [I_m x Rp], lambda double [Rp], B T [Imax x Rp],
 //           Phi[m] T [I_m x Rp] (kept for the shift S of the next iteration);
 //           FP32 form: also FP64 masters A64[m] [I_m x Rp] and B64 [Imax x Rp]
@@ -48,12 +50,15 @@ struct InnerState {
 struct ModeLayout {
     int32_t In = 0;
     int32_t *seg = nullptr;
-    int32_t *rid = nullptr;
+    uint32_t *rstart = nullptr;    // row-start bits of the sorted positions (a word per 32 nonzeros)
+    int32_t *nzrow = nullptr;      // [K] rows with nonzeros, increasing
+    int32_t K = 0;
     int32_t *idx[kMaxModes - 1] = {};
     void *val = nullptr;
     // tiles
     int32_t tile_nnz = 0, ntiles = 0, lanes = 1, reduction = CPAPR_REDUCE_SEGMENTED, threads = 256;
     int32_t *row_first = nullptr;  // [ntiles] row holding the tile's first nonzero
+    int32_t *krow = nullptr;       // [ntiles + 1] index in nzrow of that row; krow[ntiles] = K - 1
     int32_t nsplit = 0;
     int32_t *split = nullptr;      // [3 * nsplit] (row, first tile, last tile)
     int32_t *tsplit = nullptr;     // [2 * ntiles] split of each tile's head / tail partial, or -1

@@ -81,7 +81,9 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.In = L.In;
     a.nm1 = ctx->N - 1;
     a.atomic = L.reduction == CPAPR_REDUCE_ATOMIC ? 1 : 0;
-    a.rid = L.rid;
+    a.rstart = L.rstart;
+    a.nzrow = L.nzrow;
+    a.krow = L.krow;
     int k = 0;
     for (int m = 0; m < ctx->N; ++m) {
         if (m == n) continue;

@@ -25,9 +25,12 @@
 // Rows without nonzeros are never touched.  With reduction = ATOMIC, levels
 // 2 and 3 are replaced by atomic adds into a zeroed output.
 //
-// A tile's row ids, coordinates and values are first staged in shared
-// memory by bulk asynchronous copies, so that a batch reads them with a few
-// vector shared loads and only the factor-row gathers go to L1/L2.
+// A tile's coordinates and values are first staged in shared memory by bulk
+// asynchronous copies, so that a batch reads them with a few vector shared
+// loads and only the factor-row gathers go to L1/L2.  The rows are not
+// streamed per nonzero: the tile stages the row-start bits of its positions
+// (one bit per nonzero) and the list of its rows (one entry per row), and a
+// group walks its run by counting row starts.
 //
 // The KKT violation max_{i,r} |min(B, 1 - Phi)| of the MU loop is folded in:
 // whoever writes a final Phi row also reduces its violation, and one atomicMax
@@ -58,7 +61,9 @@ struct PhiArgs {
     int32_t In;
     int32_t nm1;     // number of gathered modes (N - 1)
     int32_t atomic;  // 1: partial rows are added with atomics into a zeroed output
-    const int32_t *rid;  // i_n of every nonzero in mode-n order
+    const uint32_t *rstart;  // row-start bits of the sorted positions: bit p set where a row begins at p
+    const int32_t *nzrow;    // the rows holding nonzeros, increasing
+    const int32_t *krow;     // [ntiles + 1] index in nzrow of the row holding each tile's first nonzero
     const int32_t *idx[kMaxNm1];
     const void *val;
     const void *A[kMaxNm1];
@@ -335,12 +340,18 @@ constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s
 // entries reserved per staged stream (a multiple of 4: 16-byte rows)
 __host__ __device__ constexpr int stage_cap(int T) { return (T + 3) & ~3; }
 
-// shared-memory bytes of a tile of T nonzeros: the staged streams (row ids,
-// N-1 coordinates, values) followed by the partial-row slots of the
-// segmented reduction (2 per group of lanes)
+// 32-bit words of row-start bits a tile stages (from the 16-byte group that
+// holds its first position through the word of the position after its last),
+// with room to spare; the same count holds the set bits before each word.
+__host__ __device__ constexpr int stage_words(int T) { return (((T + 31) >> 5) + 8 + 3) & ~3; }
+
+// shared-memory bytes of a tile of T nonzeros: the tile's rows, the staged
+// streams (N-1 coordinates, values), the row-start bits and their word
+// counts, then the partial-row slots of the segmented reduction (2 per group
+// of lanes) and a few words of bookkeeping
 __host__ __device__ constexpr size_t phi_smem_bytes(int T, int nm1, int esize, int threads, int rpl) {
-    return (size_t)stage_cap(T) * (size_t)(4 * (nm1 + 1) + esize) + (size_t)2 * threads * rpl * esize +
-           (size_t)2 * threads * 4 + 16;
+    return (size_t)(stage_cap(T) + 8) * 4 + (size_t)stage_cap(T) * (size_t)(4 * nm1 + esize) +
+           (size_t)stage_words(T) * 8 + (size_t)2 * threads * rpl * esize + (size_t)2 * threads * 4 + 32;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -492,24 +503,41 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     const unsigned gmask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((wlane / G) * G));
 
     const int cap = stage_cap(a.T);
-    int32_t *s_rid = reinterpret_cast<int32_t *>(smem_raw);
-    int32_t *s_idx = s_rid + cap;  // [nm1][cap]
+    const int W = stage_words(a.T);
+    int32_t *s_rows = reinterpret_cast<int32_t *>(smem_raw);  // [cap + 8]: the tile's rows (from nzrow)
+    int32_t *s_idx = s_rows + cap + 8;                          // [nm1][cap]
     T *s_val = reinterpret_cast<T *>(s_idx + (int64_t)nm1 * cap);
-    T *slot_val = s_val + cap;                                                 // [2 * NG][Rp]
+    uint32_t *s_bits = reinterpret_cast<uint32_t *>(s_val + cap);  // [W]: row-start bits from word w0
+    int32_t *s_cnt = reinterpret_cast<int32_t *>(s_bits + W);      // [W]: set bits before each staged word
+    T *slot_val = reinterpret_cast<T *>(s_cnt + W);                 // [2 * NG][Rp]
     int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
     int32_t *slot_fin = slot_row + 2 * NG;  // [2]: rows spanning tiles this block finishes
+    int32_t *s_meta = slot_fin + 2;         // [2]: s_rows index of the tile's first row; rows after it
+    // the staged bits start at the 16-byte group holding bit p0 and run
+    // through the word holding bit p1 (whether the last row goes on)
+    const int64_t w0 = (p0 >> 5) & ~(int64_t)3;
+    const int nw = (int)((((p1 >> 5) - w0 + 1) + 3) & ~(int64_t)3);
 
     // the previous tile of a persistent block may still read the stage and the slots
     __syncthreads();
     if (tid == 0) {
         // order this block's earlier generic accesses of the stage before the async writes
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the tile's rows: nzrow[k0 .. k1], k0 holding p0 and k1 holding p1
+        // (or the last row), copied from the 16-byte group holding k0
+        const int32_t k0 = __ldg(a.krow + t), k1 = __ldg(a.krow + t + 1);
+        const int32_t k0a = k0 & ~3;
+        const uint32_t br = (uint32_t)((k1 - k0a + 1 + 3) & ~3) * 4u;
+        const uint32_t bw = (uint32_t)nw * 4u;
         const uint32_t b4 = (uint32_t)(((int64_t)n * 4 + 15) & ~(int64_t)15);
         const uint32_t bv = (uint32_t)(((int64_t)n * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
-        stage_expect(bar, b4 * (uint32_t)(nm1 + 1) + bv + a.stage_extra);
-        stage_copy(s_rid, a.rid + p0, b4, bar);
+        stage_expect(bar, br + bw + b4 * (uint32_t)nm1 + bv + a.stage_extra);
+        stage_copy(s_rows, a.nzrow + k0a, br, bar);
+        stage_copy(s_bits, a.rstart + w0, bw, bar);
         for (int k = 0; k < nm1; ++k) stage_copy(s_idx + (int64_t)k * cap, a.idx[k] + p0, b4, bar);
         stage_copy(s_val, reinterpret_cast<const T *>(a.val) + p0, bv, bar);
+        s_meta[0] = k0 - k0a;
+        s_meta[1] = k1 - k0;
     }
     const bool segmented = (OP != OP_LL) && !a.atomic;
     if (segmented) {
@@ -523,6 +551,37 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         if (!landed) stage_wait(bar, phase ^ 1u);  // let the copies finish before the block moves on
         return false;
     }
+    // set bits before each staged word (one warp, a running warp scan)
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < nw; base += 32) {
+            const int w = base + wlane;
+            const int c = w < nw ? __popc(s_bits[w]) : 0;
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (wlane >= o) x += y;
+            }
+            if (w < nw) s_cnt[w] = carry + x - c;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    // row-start bit of tile position q (0 <= q <= n), and the row starts at
+    // or before it counted from the tile's first staged word
+    auto bit_at = [&](int q) -> uint32_t {
+        const int64_t p = p0 + q;
+        return (s_bits[(int)((p >> 5) - w0)] >> (int)(p & 31)) & 1u;
+    };
+    auto starts_upto = [&](int q) -> int {
+        const int64_t p = p0 + q;
+        const int wi = (int)((p >> 5) - w0);
+        return s_cnt[wi] + __popc(s_bits[wi] & (0xffffffffu >> (31 - (int)(p & 31))));
+    };
+    // s_rows index of the row holding tile position q: the tile's first row
+    // plus the row starts in (p0, p0 + q]
+    const int rbase = s_meta[0] - starts_upto(0);
 
     const T *__restrict__ Bm = reinterpret_cast<const T *>(a.B);
     T *__restrict__ out = reinterpret_cast<T *>(a.out);
@@ -555,10 +614,10 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 
     if (la < lb) {
         // does the row at la begin before the run, the row at lb - 1 go on after it?
-        auto rid_at = [&](int64_t p) -> int32_t { return (p >= p0 && p < p1) ? s_rid[p - p0] : __ldg(a.rid + p); };
-        const bool head_open = p0 + la > 0 && rid_at(p0 + la - 1) == s_rid[la];
-        const bool tail_open = p0 + lb < a.nnz && rid_at(p0 + lb) == s_rid[lb - 1];
-        int32_t cur = s_rid[la];
+        const bool head_open = p0 + la > 0 && !bit_at(la);
+        const bool tail_open = p0 + lb < a.nnz && !bit_at(lb);
+        int kcur = rbase + starts_upto(la);  // s_rows index of the current row
+        int32_t cur = s_rows[kcur];
         bool first_run = true;
         // Run accumulation (segmented, plain FMA).  FP32 interleaves two
         // accumulators so that each sums at most half of a run; the row sums
@@ -606,18 +665,39 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             int32_t rr[U];
             int32_t ii[U][MAXK];
             T xx[U];
+            bool fast;  // every nonzero of the batch in the current row (the common case)
             if constexpr (G == 1) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int qq = min(q + u, lb - 1);
-                    rr[u] = s_rid[qq];
+                    // a row starts at q + u (never at the run's first position, whose row is cur)
+                    if (q + u < lb && q + u > la && bit_at(q + u)) ++kcur;
+                    rr[u] = s_rows[kcur];
                     xx[u] = s_val[qq];
 #pragma unroll
                     for (int k = 0; k < MAXK; ++k)
                         if (k < nm1) ii[u][k] = s_idx[(int64_t)k * cap + qq];
                 }
+                fast = q + U <= lb && rr[U - 1] == cur;  // rows only increase along the run
             } else {
-                lds_u<U>(s_rid + q, rr);
+                // row starts among the batch's positions: q is a multiple of U and
+                // p0 of 4, so the batch's U bits lie in one word
+                const int64_t pq = p0 + q;
+                uint32_t starts = (s_bits[(int)((pq >> 5) - w0)] >> (int)(pq & 31)) & ((1u << U) - 1u);
+                if (q == la) starts &= ~1u;                       // the run's first row is cur
+                if (q + U > lb) starts &= (1u << (lb - q)) - 1u;  // past the run: not this group's
+                fast = q + U <= lb && starts == 0u;
+                if (!fast) {
+                    // the batch's rows: the current one, advanced at each row start
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if ((starts >> u) & 1u) ++kcur;
+                        rr[u] = s_rows[kcur];
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) rr[u] = cur;
+                }
                 lds_u<U>(s_val + q, xx);
 #pragma unroll
                 for (int k = 0; k < MAXK; ++k) {
@@ -640,8 +720,6 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                     }
                 }
             }
-            // every nonzero of the batch in the current row (the common case)
-            const bool fast = q + U <= lb && rr[U - 1] == cur;
 
             T pi[U][RPL];
             if constexpr (PI) {
@@ -786,7 +864,8 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         T *carry = reinterpret_cast<T *>(a.carry);
         T *carry_head = carry + (int64_t)t * Rp;
         T *carry_tail = carry + ((int64_t)a.ntiles + t) * Rp;
-        const int32_t next_row = p1 < a.nnz ? __ldg(a.rid + p1) : -1;  // row at the next tile's start
+        // row at the next tile's start if it goes on from this tile (nzrow[k1]), else -1
+        const int32_t next_row = (p1 < a.nnz && !bit_at(n)) ? s_rows[s_meta[0] + s_meta[1]] : -1;
         for (int s = warp; s < 2 * NG; s += NWARPS) {
             if (!(s == 0 || (s & 1))) continue;
             const int32_t crow = slot_row[s];
