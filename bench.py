@@ -69,18 +69,18 @@ L2_GATHER_GBS = 7450.0
 # changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        {"bytes": [2.8338e9, 2.8274e9, 2.7655e9], "nnz": 10_000_000,
+        {"bytes": [2747767552 + 16463872, 2743551488 + 11570176, 2667747328 + 867328], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
-        {"bytes": [202.1e6, 201.0e6, 197.4e6], "nnz": 10_000_000,
+        {"bytes": [149799936 + 9559040, 149753344 + 6729472, 150817280 + 658176], "nnz": 10_000_000,
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
-        {"bytes": [1424822784 + 13699072, 1424786944 + 11576576, 1401487616 + 978944, 1400192000 + 288000],
+        {"bytes": [1386904064 + 11420416, 1386836736 + 8222976, 1363130368 + 413952, 1361442560 + 195328],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f32", "materialised", (4, 4, 4, 4), (4096, 4096, 4096, 4096)):
-        {"bytes": [732876288 + 4610304, 732956928 + 2127616, 720758528 + 178432, 720126720 + 218624],
+        {"bytes": [694905856 + 3308032, 694909184 + 134144, 682068480 + 118528, 681385984 + 109056],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP32 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
@@ -111,12 +111,12 @@ def load_peaks() -> dict:
 def phi_bytes(dims, nnz, R, n, value_bytes, factor_bytes, materialised=False) -> float:
     """Compulsory HBM bytes of one Phi^(n).  Fused Khatri-Rao rows: the mode-n
     index and value streams, the row offsets, one read of every other factor
-    and of B, one write of Phi.  Materialised rows (the paper's Pi): the row
-    ids and values, the Pi stream (R values per nonzero), one read of B and
-    one write of Phi."""
+    and of B, one write of Phi.  Materialised rows (the paper's Pi): the
+    values, the Pi stream (R values per nonzero), the row offsets, one read
+    of B and one write of Phi."""
     N = len(dims)
     if materialised:
-        return nnz * (4 + value_bytes + R * factor_bytes) + factor_bytes * R * 2 * dims[n]
+        return nnz * (value_bytes + R * factor_bytes) + 4 * (dims[n] + 1) + factor_bytes * R * 2 * dims[n]
     other = sum(dims) - dims[n]
     return nnz * (4 * (N - 1) + value_bytes) + 4 * (dims[n] + 1) + factor_bytes * R * (other + 2 * dims[n])
 

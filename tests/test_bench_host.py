@@ -21,10 +21,10 @@ def test_byte_model_matches_hand_count():
 
 def test_byte_model_materialised_pi():
     # 3-way 1e5 x 1e5 x 1e3, 1e7 nonzeros, R = 32, FP64, mode 0, Pi streamed:
-    # 1e7 * (4 + 8 + 32*8) + 8*32*2*1e5 = 2.7312 GB; FLOPs 4R+2 per nonzero
+    # 1e7 * (8 + 32*8) + 4*(1e5 + 1) + 8*32*2*1e5 = 2.6916 GB; FLOPs 4R+2 per nonzero
     b = bench.phi_bytes((100_000, 100_000, 1_000), 10_000_000, 32, 0, 8, 8, materialised=True)
-    assert b == 10_000_000 * (12 + 256) + 8 * 32 * 2 * 100_000
-    assert abs(b / 1e9 - 2.7312) < 1e-4
+    assert b == 10_000_000 * (8 + 256) + 4 * 100_001 + 8 * 32 * 2 * 100_000
+    assert abs(b / 1e9 - 2.6916) < 1e-4
     assert bench.phi_flops(3, 10, 32, materialised=True) == 10 * (4 * 32 + 2)
     assert bench.phi_l2_bytes(3, 10, 32, 8, materialised=True) == 10 * 32 * 8
 
