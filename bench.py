@@ -128,6 +128,14 @@ def phi_flops(N, nnz, R, materialised=False) -> float:
     return nnz * (4 * R + 2) if materialised else nnz * ((N + 2) * R + 2)
 
 
+def phi_fp64_pipe_flops(N, nnz, R, materialised=False, dot_on_fp32=True) -> float:
+    """The part of phi_flops the FP64 Phi kernel runs on the FP64 pipe: with
+    the dot <B, pi> on the FP32 pipe (8 or fewer ranks per lane, eps >= 2^-43)
+    the 2R of the dot leave it, leaving the scale-add, the division and, fused,
+    the Khatri-Rao products."""
+    return phi_flops(N, nnz, R, materialised) - (nnz * 2 * R if dot_on_fp32 else 0)
+
+
 def phi_l2_bytes(N, nnz, R, factor_bytes, materialised=False) -> float:
     """Factor-row bytes gathered per Phi^(n): N-1 other rows and the B row per
     nonzero (fused); the B row alone with materialised rows."""
@@ -577,6 +585,11 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     launches, total_ms = stats[cp.K_PHI]
     byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb, mat[n]) for n in range(N))
     fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R, mat[n]) for n in range(N))
+    # FP64: the dot runs on the FP32 pipe where a lane holds 8 or fewer ranks
+    lanes = list(info.rank_lanes)[:N] if info is not None else [max(1, T.rank // 8)] * N
+    rp = info.rank_padded if info is not None else max(2, 1 << (R - 1).bit_length())
+    on32 = [rp // max(lanes[n], 1) <= 8 for n in range(N)]
+    fl64 = sum(inner_per_mode[n] * phi_fp64_pipe_flops(N, nnz, R, mat[n], on32[n]) for n in range(N))
     l2 = sum(inner_per_mode[n] * phi_l2_bytes(N, nnz, R, fb, mat[n]) for n in range(N))
     sec = total_ms / 1e3
     hbm = {"achieved": byts / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
@@ -585,12 +598,17 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     l2g["frac"] = l2g["achieved"] / l2g["peak"]
     form = "materialised Pi" if all(mat) else ("fused Pi" if not any(mat) else "mixed")
     if precision == cp.CPAPR_FP64:
-        ach = fl / sec / 1e12
+        ach = fl64 / sec / 1e12
+        dot32 = all(on32)
+        model = ("2R+2" if all(mat) else "NR+2") if dot32 else ("4R+2" if all(mat) else "(N+2)R+2")
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": f"phi_tile_kernel<double> ({form})",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                "flop_model": "4R+2 per nonzero" if all(mat) else "(N+2)R+2 per nonzero"}
+                "flop_model": f"{model} FP64 FLOPs per nonzero on the FP64 pipe"
+                              + (" (the dot's 2R run on the FP32 pipe)" if dot32 else ""),
+                "paper_flop_model": {"achieved": fl / sec / 1e12, "unit": "TFLOP/s",
+                                     "per_nonzero": "4R+2" if all(mat) else "(N+2)R+2"}}
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
                 "frac": hbm["frac"], "traffic": traffic, "kernel": f"phi_tile_kernel<float> ({form})",
@@ -857,7 +875,9 @@ def run_r_sweep(args):
             mat = [m == cp.CPAPR_PI_MATERIALISED for m in pim]
             per = pms / max(pl, 1)
             byts = sum(phi_bytes(T.dims, T.nnz, R, n, fb, fb, mat[n]) for n in range(N)) / N
-            fl = sum(phi_flops(N, T.nnz, R, mat[n]) for n in range(N)) / N
+            rp = int(info.rank_padded)
+            fl = sum(phi_fp64_pipe_flops(N, T.nnz, R, mat[n], rp // max(int(info.rank_lanes[n]), 1) <= 8)
+                     for n in range(N)) / N
             mb = sum(phi_bytes(T.dims, T.nnz, R, n, fb, fb, False) for n in range(N)) / N
             mper = mms / max(ml, 1)
             row = {"rank": R, "dtype": "f64" if prec == cp.CPAPR_FP64 else "f32",

@@ -106,6 +106,8 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.llpart = ctx->llpart;
     a.err = ctx->errflag + 3;
     a.stage_extra = injected_stage_shortfall();
+    // the FP64 dot product on the FP32 pipe is accurate relative to max(s, eps) for eps >= 2^-43
+    a.dfdot = (ctx->esize == 8 && ctx->opt.eps >= 0x1p-43) ? 1 : 0;
     return a;
 }
 

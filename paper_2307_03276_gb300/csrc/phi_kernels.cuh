@@ -85,6 +85,7 @@ struct PhiArgs {
     // log-likelihood reads where an FP32 model value underflows (else null)
     const double *Bm;
     const double *Am[kMaxNm1];
+    int32_t dfdot;  // FP64 Phi: 1 = the dot product on the FP32 pipe (df_dot; needs eps >= 2^-43)
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -142,6 +143,82 @@ __device__ __forceinline__ double phi_divide(double x, double s, double eps) {
     return x * r;
 }
 __device__ __forceinline__ float phi_divide(float x, float s, float eps) { return __fdividef(x, s > eps ? s : eps); }
+
+// ---- the FP64 form's dot product on the FP32 pipe ---------------------------------
+//
+// GB300 issues 64 FP32 FMAs for every FP64 FMA.  In the FP64 Phi kernel the dot
+// s = <B[i_n], pi> is the divisor of x and only has to be accurate relative to
+// max(s, eps), so it runs on the FP32 pipe: each FP64 operand is cut into two
+// floats hi + lo holding its leading 48 significant bits (integer operations),
+// each product hi_a hi_b is taken exactly with an FMA (Dekker's product p + e),
+// the products p are added with Knuth's two-sum (the rounding error of every
+// addition is kept), and the errors e, the cross products hi_a lo_b + lo_a hi_b
+// and the two-sum errors are summed in plain FP32.  For k terms, all >= 0,
+// with u = 2^-24 (first order):
+//   operands cut to 48 bits:                 <= 2.5 * 2^-47 s
+//   e and cross terms (3k sums of terms <= 3u s):  <= 9k u^2 s
+//   two-sum errors (k sums of terms <= u s):        <= k^2 u^2 s
+//   operands below 2^-126 dropped:           < k 2^31 2^-126 (absolute)
+// For k = 8 ranks per lane: |s_df - s| <= 5.2e-13 s + 2^-92, i.e. below 6e-13
+// relative to max(s, eps) for eps >= 2^-43, inside the FP64 form's 1e-12
+// parity bound (Phi inherits the relative error of its divisors).  An operand
+// >= 2^31 (beyond the exponents the cut assumes) makes the group redo the
+// batch with the FP64 dot.
+
+// x >= 0 as hi + lo, its leading 48 significant bits (integer operations and
+// one integer-to-float conversion); x < 2^-126 gives 0 + 0, x >= 2^31 sets big.
+__device__ __forceinline__ void df_cut(double x, float &hi, float &lo, bool &big) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const uint32_t H = (uint32_t)(bits >> 32), L = (uint32_t)bits;
+    const int e = (int)(H >> 20);  // biased exponent (x >= 0)
+    big = big || e >= 1023 + 31;
+    const bool keep = e >= 1023 - 126;
+    // hi: the first 23 fraction bits with the exponent rebased from bias 1023
+    // to bias 127 (896 less in the exponent field)
+    hi = keep ? __uint_as_float(__funnelshift_l(L, H, 3) - (896u << 23)) : 0.f;
+    // lo: the next 29 fraction bits (24 kept) times 2^(e - 1075), scaled in
+    // two exact steps that stay in the float range
+    const float m = __uint2float_rz(L & 0x1fffffffu);
+    lo = keep ? m * __uint_as_float((uint32_t)(e - 1075 + 64 + 127) << 23) * 0x1p-64f : 0.f;
+}
+
+// the float f as a double (integer operations; 0 for zero and subnormal f)
+__device__ __forceinline__ double df_widen(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const unsigned long long d = (((unsigned long long)(b & 0x7fffffffu) << 29) + (896ull << 52)) |
+                                 ((unsigned long long)(b & 0x80000000u) << 32);
+    return (b & 0x7f800000u) ? __longlong_as_double((long long)d) : 0.0;
+}
+
+// sum_r a_r b_r with a given as hi/lo floats (cut once per B row) and b in FP64
+template <int K>
+__device__ __forceinline__ double df_dot(const float (&ahi)[K], const float (&alo)[K], const double (&b)[K],
+                                         bool &big) {
+    float S = 0.f, C = 0.f, D = 0.f;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        float bh, bl;
+        df_cut(b[r], bh, bl, big);
+        const float p = ahi[r] * bh;
+        D = fmaf(ahi[r], bh, -p) + D;
+        D = fmaf(ahi[r], bl, D);
+        D = fmaf(alo[r], bh, D);
+        const float t = S + p;
+        const float z = t - S;
+        C += (S - (t - z)) + (p - z);
+        S = t;
+    }
+    return df_widen(S) + df_widen(C + D);
+}
+
+// the same with both operands in FP64
+template <int K>
+__device__ __forceinline__ double df_dot(const double (&a)[K], const double (&b)[K], bool &big) {
+    float ah[K], al[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) df_cut(a[r], ah[r], al[r], big);
+    return df_dot<K>(ah, al, b, big);
+}
 
 // On entry each of the G lanes of a group holds U partial dot products (its
 // RPL ranks) of the group's U nonzeros.  A reduce-scatter halves the set at
@@ -365,6 +442,7 @@ __device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
+
 // bytes: a multiple of 16; both addresses 16-byte aligned
 __device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -490,6 +568,13 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     constexpr int NG = THREADS / G;
     constexpr int NWARPS = THREADS / 32;
     constexpr int MAXK = NM1 > 0 ? NM1 : kMaxNm1;
+    // the tile's first and last row in nzrow, read first so that their latency
+    // passes while the block checks its state and synchronises
+    int32_t k0 = 0, k1 = 0;
+    if (threadIdx.x == 0) {
+        k0 = __ldg(a.krow + t);
+        k1 = __ldg(a.krow + t + 1);
+    }
     if (a.inner && a.inner->done) return true;
     const int nm1 = PI ? 0 : (NM1 > 0 ? NM1 : a.nm1);  // staged coordinate streams
     const int tid = threadIdx.x;
@@ -525,17 +610,16 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         // the tile's rows: nzrow[k0 .. k1], k0 holding p0 and k1 holding p1
         // (or the last row), copied from the 16-byte group holding k0
-        const int32_t k0 = __ldg(a.krow + t), k1 = __ldg(a.krow + t + 1);
         const int32_t k0a = k0 & ~3;
         const uint32_t br = (uint32_t)((k1 - k0a + 1 + 3) & ~3) * 4u;
         const uint32_t bw = (uint32_t)nw * 4u;
         const uint32_t b4 = (uint32_t)(((int64_t)n * 4 + 15) & ~(int64_t)15);
         const uint32_t bv = (uint32_t)(((int64_t)n * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
         stage_expect(bar, br + bw + b4 * (uint32_t)nm1 + bv + a.stage_extra);
-        stage_copy(s_rows, a.nzrow + k0a, br, bar);
         stage_copy(s_bits, a.rstart + w0, bw, bar);
         for (int k = 0; k < nm1; ++k) stage_copy(s_idx + (int64_t)k * cap, a.idx[k] + p0, b4, bar);
         stage_copy(s_val, reinterpret_cast<const T *>(a.val) + p0, bv, bar);
+        stage_copy(s_rows, a.nzrow + k0a, br, bar);
         s_meta[0] = k0 - k0a;
         s_meta[1] = k1 - k0;
     }
@@ -546,13 +630,9 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     }
     const bool landed = stage_wait(bar, phase);
     phase ^= 1u;
-    if (__syncthreads_or(!landed)) {
-        if (tid == 0) atomicExch(a.err, 1);
-        if (!landed) stage_wait(bar, phase ^ 1u);  // let the copies finish before the block moves on
-        return false;
-    }
-    // set bits before each staged word (one warp, a running warp scan)
-    if (warp == 0) {
+    // set bits before each staged word (one warp, a running warp scan; the
+    // block barrier below publishes them with the stage)
+    if (warp == 0 && __all_sync(0xffffffffu, landed)) {
         int carry = 0;
         for (int base = 0; base < nw; base += 32) {
             const int w = base + wlane;
@@ -567,17 +647,19 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(!landed)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        if (!landed) stage_wait(bar, phase ^ 1u);  // let the copies finish before the block moves on
+        return false;
+    }
+    // position q of the tile is bit boff + q of the staged words
+    const int boff = (int)(p0 - (w0 << 5));
     // row-start bit of tile position q (0 <= q <= n), and the row starts at
     // or before it counted from the tile's first staged word
-    auto bit_at = [&](int q) -> uint32_t {
-        const int64_t p = p0 + q;
-        return (s_bits[(int)((p >> 5) - w0)] >> (int)(p & 31)) & 1u;
-    };
+    auto bit_at = [&](int q) -> uint32_t { return (s_bits[(boff + q) >> 5] >> ((boff + q) & 31)) & 1u; };
     auto starts_upto = [&](int q) -> int {
-        const int64_t p = p0 + q;
-        const int wi = (int)((p >> 5) - w0);
-        return s_cnt[wi] + __popc(s_bits[wi] & (0xffffffffu >> (31 - (int)(p & 31))));
+        const int b = boff + q;
+        return s_cnt[b >> 5] + __popc(s_bits[b >> 5] & (0xffffffffu >> (31 - (b & 31))));
     };
     // s_rows index of the row holding tile position q: the tile's first row
     // plus the row starts in (p0, p0 + q]
@@ -610,7 +692,12 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     // lanes, whose registers go to the Khatri-Rao row and the accumulator:
     // there the dot reads the B row through L1 for every nonzero
     constexpr bool BREG = (OP != OP_MTTKRP) && !(sizeof(T) == 8 && (RPL >= 16 || U >= 4));
-    constexpr int BR = BREG ? RPL : 1;
+    // FP64 Phi with up to 8 ranks per lane takes its dot on the FP32 pipe
+    // (df_dot); a B row in registers is then kept as hi/lo floats
+    constexpr bool DFDOT = sizeof(T) == 8 && OP == OP_PHI && RPL <= 8;
+    constexpr bool BREGD = BREG && !DFDOT;  // B row in registers in the working type
+    constexpr int BR = BREGD ? RPL : 1;
+    constexpr int BF = (BREG && DFDOT) ? RPL : 1;
 
     if (la < lb) {
         // does the row at la begin before the run, the row at lb - 1 go on after it?
@@ -629,8 +716,21 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 #pragma unroll
             for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
         T brow[BR];  // B row of `brow_row` (loaded once per row, not per nonzero)
+        float bhi[BF], blo[BF];  // or that row cut into hi/lo floats (df_dot)
+        bool bbig = false;       // the cut row has an entry >= 2^31
         int32_t brow_row = cur;
-        if constexpr (BREG) load_row<T, BR>(Bm + (int64_t)cur * Rp + col0, brow);
+        auto load_brow = [&]() {
+            if constexpr (BREGD) {
+                load_row<T, BR>(Bm + (int64_t)cur * Rp + col0, brow);
+            } else if constexpr (BREG && DFDOT) {
+                T t[RPL];
+                load_row<T, RPL>(Bm + (int64_t)cur * Rp + col0, t);
+                bbig = false;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) df_cut((double)t[r], bhi[r], blo[r], bbig);
+            }
+        };
+        load_brow();
 
         auto flush = [&](int32_t frow, bool first, bool last) {
             T v[RPL];
@@ -640,7 +740,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             if (!before && !after) {
                 store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
                 if (OP == OP_PHI) {
-                    if constexpr (BREG) {
+                    if constexpr (BREGD) {
                         if (frow == brow_row) {
 #pragma unroll
                             for (int r = 0; r < RPL; ++r) kkt = tmax(kkt, viol_t(brow[r], v[r]));
@@ -667,23 +767,32 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             T xx[U];
             bool fast;  // every nonzero of the batch in the current row (the common case)
             if constexpr (G == 1) {
+                // row starts among the batch's positions (the U bits may straddle two
+                // words: one-lane runs need not start on multiples of U)
+                const int bq = boff + q;
+                uint32_t starts = __funnelshift_r(s_bits[bq >> 5], s_bits[(bq >> 5) + 1], bq & 31) & ((1u << U) - 1u);
+                if (q == la) starts &= ~1u;                       // the run's first row is cur
+                if (q + U > lb) starts &= (1u << (lb - q)) - 1u;  // past the run: not this group's
+                fast = q + U <= lb && starts == 0u;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int qq = min(q + u, lb - 1);
-                    // a row starts at q + u (never at the run's first position, whose row is cur)
-                    if (q + u < lb && q + u > la && bit_at(q + u)) ++kcur;
-                    rr[u] = s_rows[kcur];
+                    if (fast) {
+                        rr[u] = cur;
+                    } else {
+                        if ((starts >> u) & 1u) ++kcur;
+                        rr[u] = s_rows[kcur];
+                    }
                     xx[u] = s_val[qq];
 #pragma unroll
                     for (int k = 0; k < MAXK; ++k)
                         if (k < nm1) ii[u][k] = s_idx[(int64_t)k * cap + qq];
                 }
-                fast = q + U <= lb && rr[U - 1] == cur;  // rows only increase along the run
             } else {
                 // row starts among the batch's positions: q is a multiple of U and
                 // p0 of 4, so the batch's U bits lie in one word
-                const int64_t pq = p0 + q;
-                uint32_t starts = (s_bits[(int)((pq >> 5) - w0)] >> (int)(pq & 31)) & ((1u << U) - 1u);
+                const int bq = boff + q;
+                uint32_t starts = (s_bits[bq >> 5] >> (bq & 31)) & ((1u << U) - 1u);
                 if (q == la) starts &= ~1u;                       // the run's first row is cur
                 if (q + U > lb) starts &= (1u << (lb - q)) - 1u;  // past the run: not this group's
                 fast = q + U <= lb && starts == 0u;
@@ -743,14 +852,36 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                 for (int u = 0; u < U; ++u) v[u] = xx[u];
             } else {
                 T s[U];
-                if (BREG && fast) {
+                bool fp64dot = true;
+                if constexpr (DFDOT) {
+                    if (a.dfdot) {
+                        // <B[i_n], pi> on the FP32 pipe; each lane's partial in FP64
+                        bool big = false;
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if constexpr (BREG) s[u] = dot_regs<T, RPL>(brow, pi[u]);
+                        for (int u = 0; u < U; ++u) {
+                            if (BREG && fast) {
+                                if constexpr (BREG) s[u] = (T)df_dot<RPL>(bhi, blo, pi[u], big);
+                            } else {
+                                T brw[RPL];
+                                load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, brw);
+                                s[u] = (T)df_dot<RPL>(brw, pi[u], big);
+                            }
+                        }
+                        if constexpr (BREG) big = big || (fast && bbig);
+                        fp64dot = __any_sync(gmask, big);
                     }
-                } else {
+                }
+                if (fp64dot) {
+                    if (BREGD && fast) {
 #pragma unroll
-                    for (int u = 0; u < U; ++u) s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
+                        for (int u = 0; u < U; ++u) {
+                            if constexpr (BREGD) s[u] = dot_regs<T, RPL>(brow, pi[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
+                    }
                 }
                 if constexpr (G == 1) {
 #pragma unroll
@@ -834,7 +965,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                 }
                 if constexpr (BREG) {
                     if (cur != brow_row) {
-                        load_row<T, BR>(Bm + (int64_t)cur * Rp + col0, brow);
+                        load_brow();
                         brow_row = cur;
                     }
                 }

@@ -742,3 +742,27 @@ def test_tune_cache_ignores_lines_that_do_not_fit(tmp_path):
         t.set_model(lam, fs)
         want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[0] * lam[None, :], 0)
         assert max_rel(t.phi(0), want) <= 1e-12
+
+
+@pytest.mark.parametrize("pi_mode", PI_MODES)
+def test_fp64_dot_fallbacks_match_oracle(pi_mode):
+    """The FP64 form takes the dot <B, pi> on the FP32 pipe (operands cut into
+    48-bit hi/lo float pairs).  Where an operand is 2^31 or more the group
+    redoes its batch with the FP64 dot, and with eps below 2^-43 the FP64 dot
+    is used throughout; both paths against the oracle at the FP64 bound, with
+    B entries spread from 1e-40 to 1e12."""
+    T = case("c3s")
+    lam, fs = model_for(T, 31)
+    rng = np.random.default_rng(5)
+    for n in range(T.nmodes):
+        B = fs[n] * 10.0 ** rng.uniform(-30, 12, size=fs[n].shape)
+        B[::7, 0] = 2.0 ** 40  # rows whose batches fall back to the FP64 dot
+        B[1::11, 1] = 1e-40    # entries below the float range (dropped parts)
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode) as t:
+            t.set_model(lam, fs)
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n)
+            assert max_rel(t.phi(n, B=B), want) <= 1e-12, n
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode, eps=1e-20) as t:
+            t.set_model(lam, fs)
+            want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n, eps=1e-20)
+            assert max_rel(t.phi(n, B=B), want) <= 1e-12, n
