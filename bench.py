@@ -69,13 +69,13 @@ L2_GATHER_GBS = 7450.0
 # changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        {"bytes": [2747767552 + 16463872, 2743551488 + 11570176, 2667747328 + 867328], "nnz": 10_000_000,
+        {"bytes": [2668592384 + 16397824, 2667578112 + 11703552, 2641807104 + 883712], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
         {"bytes": [149799936 + 9559040, 149753344 + 6729472, 150817280 + 658176], "nnz": 10_000_000,
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
-        {"bytes": [1386904064 + 11420416, 1386836736 + 8222976, 1363130368 + 413952, 1361442560 + 195328],
+        {"bytes": [1386888960 + 11494656, 1386825984 + 8386304, 1362806016 + 366592, 1361464320 + 183296],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},

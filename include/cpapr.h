@@ -53,6 +53,7 @@ typedef enum {
 enum { CPAPR_FP64 = 0, CPAPR_FP32 = 1 };
 enum { CPAPR_REDUCE_AUTO = 0, CPAPR_REDUCE_ATOMIC = 1, CPAPR_REDUCE_SEGMENTED = 2 };
 enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
+enum { CPAPR_DOT_AUTO = 0, CPAPR_DOT_FP64 = 1, CPAPR_DOT_FP32_PIPE = 2 };
 
 /*
  * Options.  Fill with cpapr_default_options() and change what you need.
@@ -84,6 +85,17 @@ enum { CPAPR_PI_AUTO = 0, CPAPR_PI_FUSED = 1, CPAPR_PI_MATERIALISED = 2 };
  *             its KKT reduction, and for atomic adds the zeroing and the
  *             separate KKT pass they need).  Timing replaces the model; set
  *             one after cpapr_create.
+ *  fp64_dot   how the FP64 form's Phi evaluates the divisor's dot product
+ *             <B[i_n], pi>.  CPAPR_DOT_FP64: FP64 FMAs.  CPAPR_DOT_FP32_PIPE:
+ *             on the FP32 pipe (64 times the FP64 FMA rate on GB300) with
+ *             error-free transformations of 48-bit hi/lo cuts of the FP64
+ *             operands; its error stays below 6e-13 relative to
+ *             max(s, eps), inside the FP64 form's 1e-12 bound (it applies to
+ *             lanes of 8 or fewer ranks and eps >= 2^-43; operands >= 2^31 take
+ *             the FP64 dot for their batch).  CPAPR_DOT_AUTO (default): the FP32
+ *             pipe where a launch has at least 608 tiles (4 per SM), the FP64
+ *             dot below that, where one tile's latency bounds the launch.  The
+ *             batched solver always takes the FP64 dot.  Ignored in FP32.
  *  tune_cache NULL (default) or the path of a text file of tuned choices,
  *             one line per shape class: precision, number of modes, padded
  *             rank, and power-of-two buckets of the nonzeros, of the mode's
@@ -134,7 +146,7 @@ typedef struct {
     int32_t profile;
     int32_t pi_mode;
     int32_t l2_persist;
-    int32_t reserved;
+    int32_t fp64_dot;
     const char *tune_cache;
 } cpapr_options;
 

@@ -21,6 +21,7 @@ MAX_MODES = 8
 CPAPR_FP64, CPAPR_FP32 = 0, 1
 CPAPR_REDUCE_AUTO, CPAPR_REDUCE_ATOMIC, CPAPR_REDUCE_SEGMENTED = 0, 1, 2
 CPAPR_PI_AUTO, CPAPR_PI_FUSED, CPAPR_PI_MATERIALISED = 0, 1, 2
+CPAPR_DOT_AUTO, CPAPR_DOT_FP64, CPAPR_DOT_FP32_PIPE = 0, 1, 2
 K_PHI, K_PI, K_UPDATE, K_NORM, K_SB, K_LL, K_MTTKRP = range(7)
 
 STATUS = {0: "CPAPR_OK", 1: "CPAPR_E_ARG", 2: "CPAPR_E_RANGE", 3: "CPAPR_E_VALUE", 4: "CPAPR_E_NOMEM",
@@ -41,7 +42,7 @@ class Options(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("kappa_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile_nnz", ctypes.c_int32), ("rank_lanes", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("pi_mode", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pi_mode", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("fp64_dot", ctypes.c_int32),
                 ("tune_cache", ctypes.c_char_p)]
 
 

@@ -398,6 +398,8 @@ cpapr_status cpapr_create(int32_t nmodes, const int64_t *dims, int64_t nnz, cons
     if (o.tile_nnz != 0 && (o.tile_nnz < 64 || o.tile_nnz > (1 << 20) || o.tile_nnz % 4))
         return fail(nullptr, CPAPR_E_ARG, "tile_nnz must be 0 or a multiple of 4 in [64, 2^20]");
     if (o.l2_persist != 0 && o.l2_persist != 1) return fail(nullptr, CPAPR_E_ARG, "l2_persist must be 0 or 1");
+    if (o.fp64_dot < CPAPR_DOT_AUTO || o.fp64_dot > CPAPR_DOT_FP32_PIPE)
+        return fail(nullptr, CPAPR_E_ARG, "fp64_dot must be CPAPR_DOT_AUTO, CPAPR_DOT_FP64 or CPAPR_DOT_FP32_PIPE");
 
     cpapr_ctx *ctx = new (std::nothrow) cpapr_ctx();
     if (!ctx) return fail(nullptr, CPAPR_E_NOMEM, "host allocation failed");

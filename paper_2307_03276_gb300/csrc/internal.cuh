@@ -137,6 +137,8 @@ struct cpapr_ctx {
 namespace cpapr {
 
 constexpr int kColParts = 256;
+// tiles from which an FP64 Phi launch takes the kernel with its dot on the FP32 pipe
+constexpr int kDfMinTiles = 152 * 4;
 
 // ---- error plumbing ------------------------------------------------------
 cpapr_status fail(cpapr_ctx *ctx, cpapr_status st, const std::string &msg);

@@ -106,8 +106,15 @@ static PhiArgs make_args(cpapr_ctx *ctx, int n, const void *B, void *out, InnerS
     a.llpart = ctx->llpart;
     a.err = ctx->errflag + 3;
     a.stage_extra = injected_stage_shortfall();
-    // the FP64 dot product on the FP32 pipe is accurate relative to max(s, eps) for eps >= 2^-43
-    a.dfdot = (ctx->esize == 8 && ctx->opt.eps >= 0x1p-43) ? 1 : 0;
+    // FP64 Phi with its dot product on the FP32 pipe: accurate relative to
+    // max(s, eps) for eps >= 2^-43, and faster where the launch has at least a
+    // wave of tiles (4 per SM); a launch of a few tiles is bound by one
+    // tile's latency, which the longer FP32 instruction chains raise
+    const int dot = ctx->opt.fp64_dot;
+    a.dfdot = (ctx->esize == 8 && ctx->opt.eps >= 0x1p-43 &&
+               (dot == CPAPR_DOT_FP32_PIPE || (dot == CPAPR_DOT_AUTO && L.ntiles >= kDfMinTiles)))
+                  ? 1
+                  : 0;
     return a;
 }
 

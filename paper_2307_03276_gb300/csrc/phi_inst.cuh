@@ -21,10 +21,13 @@ constexpr int kThreads = sizeof(PHI_T) == 8 ? 128 : 256;
 // nonzeros per batch (U <= G when G > 1: after the reduce-scatter every lane
 // finishes one of them, so a nonzero costs G / U divisions; one lane per
 // nonzero takes two at a time for memory-level parallelism).  FP64 at 16
-// ranks per lane has no registers to spare for a second batch entry.
+// ranks per lane has no registers to spare for a second batch entry; FP64 at
+// 8 or fewer takes two: with four its kernel with the dot on the FP32 pipe
+// needed 178 registers and ran 37% slower on the 3-way tensor (1.63 vs 1.19
+// ms on GB300), and both kernels share the batch size.
 template <int RPL, int G>
 constexpr int unroll_for() {
-    if (sizeof(PHI_T) == 8) return RPL >= 16 ? (G >= 2 ? 2 : 1) : (G >= 4 ? 4 : 2);
+    if (sizeof(PHI_T) == 8) return RPL >= 16 ? (G >= 2 ? 2 : 1) : 2;
     return G >= 4 ? 4 : 2;
 }
 
@@ -59,10 +62,16 @@ cudaError_t run(const PhiArgs &a, cudaStream_t s, const cudaAccessPolicyWindow *
     constexpr int U = unroll_for<RPL, G>();
     // the log-likelihood's underflow fallback needs more registers than four
     // blocks per SM allow (measured: 7% faster unconstrained)
-    if constexpr (phi_occ4<PHI_T, RPL>() && OP != OP_LL)
+    if constexpr (phi_occ4<PHI_T, RPL>() && OP != OP_LL) {
         return launch<RPL>(phi_tile_kernel_occ4<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
-    else
+    } else {
+        // FP64 Phi with 8 or fewer ranks per lane: the launcher's choice of the
+        // kernel that takes the dot on the FP32 pipe
+        if constexpr (sizeof(PHI_T) == 8 && OP == OP_PHI && RPL <= 8) {
+            if (a.dfdot) return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI, true>, a, s, win);
+        }
         return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
+    }
 }
 // log-likelihood: FP64 can stream the materialised rows, FP32 always gathers
 template <int RPL, int G>

@@ -85,7 +85,7 @@ struct PhiArgs {
     // log-likelihood reads where an FP32 model value underflows (else null)
     const double *Bm;
     const double *Am[kMaxNm1];
-    int32_t dfdot;  // FP64 Phi: 1 = the dot product on the FP32 pipe (df_dot; needs eps >= 2^-43)
+    int32_t dfdot;  // FP64 Phi: 1 = the kernel with the dot product on the FP32 pipe (df_dot)
 };
 
 // ---- compensated sums --------------------------------------------------------
@@ -559,7 +559,8 @@ __device__ __forceinline__ double dot_fp64(const PhiArgs &a, const int32_t (&ii)
 // PI: the Khatri-Rao rows are read from the materialised Pi (a.pi, one row
 // per nonzero in mode-n order) instead of being formed from the factors; the
 // stage then holds only the row ids and the values.
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI = false>
+// DF: the FP64 Phi (8 or fewer ranks per lane) takes its dot on the FP32 pipe.
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI = false, bool DF = false>
 __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, unsigned char *smem_raw, double *red,
                                               uint64_t *bar, uint32_t &phase) {
     static_assert(U == 1 || U == 2 || U == 4, "batches of 1, 2 or 4 nonzeros");
@@ -692,9 +693,9 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     // lanes, whose registers go to the Khatri-Rao row and the accumulator:
     // there the dot reads the B row through L1 for every nonzero
     constexpr bool BREG = (OP != OP_MTTKRP) && !(sizeof(T) == 8 && (RPL >= 16 || U >= 4));
-    // FP64 Phi with up to 8 ranks per lane takes its dot on the FP32 pipe
+    // FP64 Phi with up to 8 ranks per lane may take its dot on the FP32 pipe
     // (df_dot); a B row in registers is then kept as hi/lo floats
-    constexpr bool DFDOT = sizeof(T) == 8 && OP == OP_PHI && RPL <= 8;
+    constexpr bool DFDOT = DF && sizeof(T) == 8 && OP == OP_PHI && RPL <= 8;
     constexpr bool BREGD = BREG && !DFDOT;  // B row in registers in the working type
     constexpr int BR = BREGD ? RPL : 1;
     constexpr int BF = (BREG && DFDOT) ? RPL : 1;
@@ -854,7 +855,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                 T s[U];
                 bool fp64dot = true;
                 if constexpr (DFDOT) {
-                    if (a.dfdot) {
+                    {
                         // <B[i_n], pi> on the FP32 pipe; each lane's partial in FP64
                         bool big = false;
 #pragma unroll
@@ -1094,7 +1095,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 }
 
 // One block per tile of one tensor.
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI>
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI, bool DF = false>
 __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[THREADS / 32];
@@ -1102,7 +1103,7 @@ __global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     if (threadIdx.x == 0) stage_barrier_init(&bar);
     __syncthreads();
     uint32_t phase = 0;
-    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI>(a, blockIdx.x, smem_raw, red, &bar, phase);
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI, DF>(a, blockIdx.x, smem_raw, red, &bar, phase);
 }
 
 // The same with registers held to four resident blocks per SM (64 per

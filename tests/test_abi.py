@@ -90,3 +90,6 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     with pytest.raises(cpapr.CpaprError) as e:
         cpapr.cpapr_create([3, 3, 3], idx, vals, 2, cpapr.cpapr_default_options(l2_persist=2))
     assert e.value.status == 1
+    with pytest.raises(cpapr.CpaprError) as e:
+        cpapr.cpapr_create([3, 3, 3], idx, vals, 2, cpapr.cpapr_default_options(fp64_dot=3))
+    assert e.value.status == 1

@@ -72,15 +72,19 @@ CASES = ["c1", "c2s", "c3s", "c5s", "c5s64", "n2", "n6"]
 
 
 PI_MODES = [cpapr.CPAPR_PI_FUSED, cpapr.CPAPR_PI_MATERIALISED]
+# the FP64 form's dot product in FP64 and on the FP32 pipe (the automatic
+# choice picks the latter only for launches of 608 tiles or more)
+DOTS = [cpapr.CPAPR_DOT_FP64, cpapr.CPAPR_DOT_FP32_PIPE]
 
 
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("reduction", [cpapr.CPAPR_REDUCE_SEGMENTED, cpapr.CPAPR_REDUCE_ATOMIC])
 @pytest.mark.parametrize("pi_mode", PI_MODES)
-def test_phi_fp64_matches_oracle(name, reduction, pi_mode):
+@pytest.mark.parametrize("dot", DOTS)
+def test_phi_fp64_matches_oracle(name, reduction, pi_mode, dot):
     T = case(name)
     lam, fs = model_for(T)
-    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, reduction=reduction, pi_mode=pi_mode) as t:
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, reduction=reduction, pi_mode=pi_mode, fp64_dot=dot) as t:
         t.set_model(lam, fs)
         for n in range(T.nmodes):
             want = oracle.phi(T.dims, T.idx, T.vals, fs, fs[n] * lam[None, :], n)
@@ -90,7 +94,7 @@ def test_phi_fp64_matches_oracle(name, reduction, pi_mode):
 
 @pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c5s64"])
 @pytest.mark.parametrize("tile", [64, 320, 4096])
-def test_phi_fp64_tile_sizes(name, tile):
+def test_phi_fp64_tile_sizes(name, tile):  # 64-nonzero tiles: 608 or more tiles, the FP32-pipe dot
     """Small tiles cut many rows across tiles and groups (rows finished by the
     last tile to arrive), large ones few."""
     T = case(name)
@@ -202,12 +206,13 @@ def test_phi_deterministic_segmented():
 
 
 @pytest.mark.parametrize("use_graph", [0, 1])
-def test_mu_solve_fp64_matches_oracle_c1(use_graph):
+@pytest.mark.parametrize("dot", DOTS)
+def test_mu_solve_fp64_matches_oracle_c1(use_graph, dot):
     """Ten outer iterations of Algorithm 1 on the 100x80x60 tensor."""
     T = case("c1")
     lam, fs = model_for(T, 21)
     ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=10, max_inner=10)
-    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, use_graph=use_graph) as t:
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, use_graph=use_graph, fp64_dot=dot) as t:
         t.set_model(lam, fs)
         res = t.mu_solve(tol=1e-4, max_outer=10, max_inner=10, trace=True)
         lam_g, fs_g = t.get_model()
@@ -235,15 +240,17 @@ def test_mu_solve_fp64_4way_two_outer():
         np.testing.assert_allclose(A, Ar, rtol=1e-9, atol=1e-14 * Ar.max())
 
 
-def test_mu_solve_fp64_long_horizon():
+@pytest.mark.parametrize("dot", DOTS)
+def test_mu_solve_fp64_long_horizon(dot):
     """Twelve outer iterations of ten inner iterations on the 200,000-nonzero
     3-way Zipf tensor: the log-likelihood after every outer iteration, the
     final KKT violation and the model follow the oracle's trajectory (no
-    drift: the two agree to a few ulps after 360 Phi evaluations)."""
+    drift: the two agree to a few ulps after 360 Phi evaluations), with the
+    dot in FP64 and on the FP32 pipe."""
     T = case("c2s")
     lam, fs = model_for(T, 23)
     ref = oracle.mu_solve(T.dims, T.idx, T.vals, lam, fs, tol=1e-4, max_outer=12, max_inner=10)
-    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank) as t:
+    with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, fp64_dot=dot) as t:
         t.set_model(lam, fs)
         res = t.mu_solve(tol=1e-4, max_outer=12, max_inner=10, trace=True, ll_trace=True)
         lam_g, fs_g = t.get_model()
@@ -439,7 +446,8 @@ def test_materialised_pi_equals_fused(name, precision):
     lam, fs = model_for(T, 12)
     got = {}
     for pm in PI_MODES:
-        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, pi_mode=pm, tile_nnz=1024) as t:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, precision=precision, pi_mode=pm, tile_nnz=1024,
+                          fp64_dot=cpapr.CPAPR_DOT_FP32_PIPE) as t:
             t.set_model(lam, fs)
             info = t.info()
             assert list(info.pi_mode)[:T.nmodes] == [pm] * T.nmodes
@@ -758,11 +766,12 @@ def test_fp64_dot_fallbacks_match_oracle(pi_mode):
         B = fs[n] * 10.0 ** rng.uniform(-30, 12, size=fs[n].shape)
         B[::7, 0] = 2.0 ** 40  # rows whose batches fall back to the FP64 dot
         B[1::11, 1] = 1e-40    # entries below the float range (dropped parts)
-        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode) as t:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode, fp64_dot=cpapr.CPAPR_DOT_FP32_PIPE) as t:
             t.set_model(lam, fs)
             want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n)
             assert max_rel(t.phi(n, B=B), want) <= 1e-12, n
-        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode, eps=1e-20) as t:
+        with cpapr.Tensor(T.dims, T.idx, T.vals, T.rank, pi_mode=pi_mode, eps=1e-20,
+                          fp64_dot=cpapr.CPAPR_DOT_FP32_PIPE) as t:
             t.set_model(lam, fs)
             want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n, eps=1e-20)
             assert max_rel(t.phi(n, B=B), want) <= 1e-12, n
