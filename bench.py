@@ -808,11 +808,12 @@ def run_kernel_only(args):
         print(json.dumps({"kernel": "batch", "precision": args.precision, "workload": "c4_batch64_3way",
                           "outer_iterations": args.steps, "inner_iterations": inner}))
         return
-    if args.nnz:
-        # the same workload with fewer nonzeros (same dims, rank and
-        # distributions): a capture target of a few GB for ncu
+    if args.nnz or args.rank:
+        # the same workload with fewer nonzeros (same dims and distributions)
+        # and/or another rank: a capture target of a few GB for ncu
         from paper_2307_03276_gb300 import synth
-        spec = synth.scaled(synth.SPECS[args.workload], args.nnz)
+        base = synth.SPECS[args.workload]
+        spec = synth.scaled(base, args.nnz or base.nnz, rank=args.rank or None)
         T = synth.generate(spec)
         lam, fs = np.ones(T.rank), synth.random_factors(T.dims, T.rank, spec.seed + 17)
     else:
@@ -824,7 +825,7 @@ def run_kernel_only(args):
                 t.phi(n)
         launches, ms = t.kernel_stats(cp.K_PHI)
         info = t.info()
-    print(json.dumps({"kernel": "phi_tile_kernel", "precision": args.precision, "workload": T.name,
+    print(json.dumps({"kernel": "phi_tile_kernel", "precision": args.precision, "workload": T.name, "rank": T.rank,
                       "nnz": T.nnz, "pi_mode": list(info.pi_mode)[:T.nmodes],
                       "launches": launches, "avg_ms": ms / max(launches, 1),
                       "tile_nnz": list(info.tile_nnz)[:T.nmodes], "rank_lanes": list(info.rank_lanes)[:T.nmodes]}))
@@ -1031,6 +1032,7 @@ def main(argv=None):
                     help="only run Phi^(n) for every mode --steps times (profiling target)")
     ap.add_argument("--nnz", type=int, default=0,
                     help="with --kernel-only: the workload scaled to this many nonzeros (same dims)")
+    ap.add_argument("--rank", type=int, default=0, help="with --kernel-only: the workload at this rank")
     ap.add_argument("--time-to-kkt", action="store_true",
                     help="full solve at KKT tolerance 1e-4 (FP64 and FP32) on --workload")
     ap.add_argument("--max-outer", type=int, default=KKT_MAX_OUTER)
