@@ -69,18 +69,18 @@ L2_GATHER_GBS = 7450.0
 # changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        {"bytes": [2668592384 + 16397824, 2667578112 + 11703552, 2641807104 + 883712], "nnz": 10_000_000,
+        {"bytes": [2667572480 + 16308736, 2667997952 + 11258880, 2641735424 + 850432], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
-        {"bytes": [149799936 + 9559040, 149753344 + 6729472, 150817280 + 658176], "nnz": 10_000_000,
+        {"bytes": [150059520 + 9511424, 149919744 + 6664704, 150980608 + 513792], "nnz": 10_000_000,
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
-        {"bytes": [1386888960 + 11494656, 1386825984 + 8386304, 1362806016 + 366592, 1361464320 + 183296],
+        {"bytes": [1386854912 + 11519232, 1386826496 + 8379904, 1363041024 + 544256, 1361456128 + 181248],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f32", "materialised", (4, 4, 4, 4), (4096, 4096, 4096, 4096)):
-        {"bytes": [694905856 + 3308032, 694909184 + 134144, 682068480 + 118528, 681385984 + 109056],
+        {"bytes": [694901248 + 3416832, 694904832 + 191488, 682061568 + 286720, 681378304 + 224000],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP32 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
@@ -88,9 +88,10 @@ NCU_TRAFFIC = {
 
 
 def layout_bytes(T) -> int:
-    """Bytes of the per-mode sorted layouts (row ids, the other modes'
-    coordinates, FP64 values) that every step streams."""
-    return T.nmodes * T.nnz * (4 + 4 * (T.nmodes - 1) + 8)
+    """Bytes of the per-mode sorted layouts that every step streams: the other
+    modes' int32 coordinates, the FP64 values and one row-start bit per
+    nonzero, for each mode."""
+    return T.nmodes * (T.nnz * (4 * (T.nmodes - 1) + 8) + T.nnz // 8)
 
 
 def load_peaks() -> dict:
@@ -136,10 +137,12 @@ def phi_fp64_pipe_flops(N, nnz, R, materialised=False, dot_on_fp32=True) -> floa
     return phi_flops(N, nnz, R, materialised) - (nnz * 2 * R if dot_on_fp32 else 0)
 
 
-def phi_l2_bytes(N, nnz, R, factor_bytes, materialised=False) -> float:
-    """Factor-row bytes gathered per Phi^(n): N-1 other rows and the B row per
-    nonzero (fused); the B row alone with materialised rows."""
-    return nnz * (1 if materialised else N) * R * factor_bytes
+def phi_gather_bytes(N, nnz, R, factor_bytes, materialised=False) -> float:
+    """Factor-row bytes the Phi walk gathers per launch: the N-1 other modes'
+    rows per nonzero with fused Khatri-Rao rows; none with materialised rows
+    (those are streamed).  The B row is read once per run of a row and kept in
+    registers along it, so it is not counted."""
+    return 0.0 if materialised else float(nnz) * (N - 1) * R * factor_bytes
 
 
 # ---------------------------------------------------------------------------
@@ -558,20 +561,26 @@ def kernel_breakdown(stats, steps):
 def ncu_traffic(T, dtype, mat, info, inner_per_mode):
     """Measured DRAM bytes per Phi launch for this configuration (scaled to the
     tensor's nonzeros where the capture ran on a smaller copy), weighted by the
-    launches of each mode, with its source; (None, None) if not captured."""
+    launches of each mode, with its source and, where captured, the L2 bytes
+    read by L1 misses per launch; (None, None, None) if not captured."""
     N = T.nmodes
     form = "materialised" if all(mat) else ("fused" if not any(mat) else "mixed")
     key = (T.name, dtype, form, tuple(info.rank_lanes)[:N], tuple(info.tile_nnz)[:N])
     if key not in NCU_TRAFFIC:
-        return None, None
+        return None, None, None
     ent = NCU_TRAFFIC[key]
     fb = 8 if dtype == "f64" else 4
+    scale = T.nnz / ent["nnz"]
     per_mode = []
     for n in range(N):
         io = 2.0 * T.rank * fb * T.dims[n]
-        per_mode.append((ent["bytes"][n] - io) * T.nnz / ent["nnz"] + io)
+        per_mode.append((ent["bytes"][n] - io) * scale + io)
     w = [float(inner_per_mode[n]) for n in range(N)]
-    return sum(w[n] * per_mode[n] for n in range(N)) / max(sum(w), 1.0), ent["source"]
+    tot = max(sum(w), 1.0)
+    l2 = None
+    if "l2_read" in ent:
+        l2 = sum(w[n] * ent["l2_read"][n] * scale for n in range(N)) / tot
+    return sum(w[n] * per_mode[n] for n in range(N)) / tot, ent["source"], l2
 
 
 def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, info=None):
@@ -580,8 +589,8 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     N, nnz, R = T.nmodes, T.nnz, T.rank
     fb = 8 if precision == cp.CPAPR_FP64 else 4
     mat = [bool(pi_modes and pi_modes[n] == cp.CPAPR_PI_MATERIALISED) for n in range(N)]
-    traffic, traffic_src = (ncu_traffic(T, "f64" if fb == 8 else "f32", mat, info, inner_per_mode)
-                            if info is not None else (None, None))
+    traffic, traffic_src, l2_read = (ncu_traffic(T, "f64" if fb == 8 else "f32", mat, info, inner_per_mode)
+                                     if info is not None else (None, None, None))
     launches, total_ms = stats[cp.K_PHI]
     byts = sum(inner_per_mode[n] * phi_bytes(T.dims, nnz, R, n, fb, fb, mat[n]) for n in range(N))
     fl = sum(inner_per_mode[n] * phi_flops(N, nnz, R, mat[n]) for n in range(N))
@@ -590,12 +599,19 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     rp = info.rank_padded if info is not None else max(2, 1 << (R - 1).bit_length())
     on32 = [rp // max(lanes[n], 1) <= 8 for n in range(N)]
     fl64 = sum(inner_per_mode[n] * phi_fp64_pipe_flops(N, nnz, R, mat[n], on32[n]) for n in range(N))
-    l2 = sum(inner_per_mode[n] * phi_l2_bytes(N, nnz, R, fb, mat[n]) for n in range(N))
+    gath = sum(inner_per_mode[n] * phi_gather_bytes(N, nnz, R, fb, mat[n]) for n in range(N))
     sec = total_ms / 1e3
     hbm = {"achieved": byts / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
-    l2g = {"achieved": l2 / sec / 1e9, "peak": L2_GATHER_GBS, "unit": "GB/s"}
-    l2g["frac"] = l2g["achieved"] / l2g["peak"]
+    l2g = None
+    if gath > 0:
+        # gathered rows include the L1's hits; the ceiling is for rows the L2 serves, so the
+        # fraction uses the L2 sectors that ncu counted for this configuration (null if not captured)
+        l2g = {"gathered": gath / sec / 1e9, "l2_served": None, "peak": L2_GATHER_GBS, "unit": "GB/s",
+               "frac": None}
+        if l2_read is not None:
+            l2g["l2_served"] = l2_read / (total_ms / max(launches, 1) / 1e3) / 1e9
+            l2g["frac"] = l2g["l2_served"] / L2_GATHER_GBS
     form = "materialised Pi" if all(mat) else ("fused Pi" if not any(mat) else "mixed")
     if precision == cp.CPAPR_FP64:
         ach = fl64 / sec / 1e12
@@ -619,7 +635,8 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     roof["avg_launch_ms"] = total_ms / max(launches, 1)
     roof["launches"] = launches
     roof["hbm"] = hbm
-    roof["l2_gather"] = l2g
+    if l2g is not None:
+        roof["l2_gather"] = l2g
     # the paper's word count Q = nnz(5R+2) 8-byte words per Phi (Eq. "Q"), which
     # counts every factor access whether it hits a cache or not: context only
     qb = sum(inner_per_mode[n] * nnz * (5 * R + 2) * 8.0 for n in range(N))

@@ -16,7 +16,7 @@ def test_byte_model_matches_hand_count():
     assert b == 50_000_000 * 20 + 4 * 200_001 + 8 * 16 * (210_365 + 400_000)
     assert abs(b / 1e9 - 1.0789) < 1e-3
     assert bench.phi_flops(4, 10, 16) == 10 * (6 * 16 + 2)
-    assert bench.phi_l2_bytes(3, 10, 32, 4) == 10 * 3 * 32 * 4
+    assert bench.phi_gather_bytes(3, 10, 32, 4) == 10 * 2 * 32 * 4
 
 
 def test_byte_model_materialised_pi():
@@ -26,7 +26,7 @@ def test_byte_model_materialised_pi():
     assert b == 10_000_000 * (8 + 256) + 4 * 100_001 + 8 * 32 * 2 * 100_000
     assert abs(b / 1e9 - 2.6916) < 1e-4
     assert bench.phi_flops(3, 10, 32, materialised=True) == 10 * (4 * 32 + 2)
-    assert bench.phi_l2_bytes(3, 10, 32, 8, materialised=True) == 10 * 32 * 8
+    assert bench.phi_gather_bytes(3, 10, 32, 8, materialised=True) == 0
 
 
 def _free_port():
