@@ -160,10 +160,14 @@ __device__ __forceinline__ float phi_divide(float x, float s, float eps) { retur
 //   two-sum errors (k sums of terms <= u s):        <= k^2 u^2 s
 //   operands below 2^-126 dropped:           < k 2^31 2^-126 (absolute)
 // For k = 8 ranks per lane: |s_df - s| <= 5.2e-13 s + 2^-92, i.e. below 6e-13
-// relative to max(s, eps) for eps >= 2^-43, inside the FP64 form's 1e-12
-// parity bound (Phi inherits the relative error of its divisors).  An operand
-// >= 2^31 (beyond the exponents the cut assumes) makes the group redo the
-// batch with the FP64 dot.
+// relative to max(s, eps) for eps >= 2^-43.  The lanes' partials are added
+// as hi/lo pairs (df_add) and x / max(s, eps) is taken on the FP32 pipe as well
+// (df_divide, within 2^-43 relative), so v = x / max(s, eps) is within 7.5e-13
+// relative, inside the FP64 form's 1e-12 parity bound (Phi inherits the
+// relative error of its v, its terms being >= 0); the batch's FP64 operations
+// are one addition per division and the scale-add.  An operand >= 2^31
+// (beyond the exponents the cut assumes) or a value x outside {0} and
+// [2^-20, 2^31) makes the group redo the batch with the FP64 dot and division.
 
 // x >= 0 as hi + lo, its leading 48 significant bits (integer operations and
 // one integer-to-float conversion); x < 2^-126 gives 0 + 0, x >= 2^31 sets big.
@@ -190,9 +194,20 @@ __device__ __forceinline__ double df_widen(float f) {
     return (b & 0x7f800000u) ? __longlong_as_double((long long)d) : 0.0;
 }
 
-// sum_r a_r b_r with a given as hi/lo floats (cut once per B row) and b in FP64
+// a + b for hi/lo float pairs with |lo| <= ulp(hi) / 2 (Knuth's two-sum of the
+// highs, then a fast two-sum that renormalises); the result is such a pair
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float z = s - a.x;
+    const float e = ((a.x - (s - z)) + (b.x - z)) + (a.y + b.y);
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
+// sum_r a_r b_r with a given as hi/lo floats (cut once per B row) and b in
+// FP64, as a renormalised hi/lo float pair
 template <int K>
-__device__ __forceinline__ double df_dot(const float (&ahi)[K], const float (&alo)[K], const double (&b)[K],
+__device__ __forceinline__ float2 df_dot(const float (&ahi)[K], const float (&alo)[K], const double (&b)[K],
                                          bool &big) {
     float S = 0.f, C = 0.f, D = 0.f;
 #pragma unroll
@@ -208,16 +223,75 @@ __device__ __forceinline__ double df_dot(const float (&ahi)[K], const float (&al
         C += (S - (t - z)) + (p - z);
         S = t;
     }
-    return df_widen(S) + df_widen(C + D);
+    const float E = C + D;
+    const float h = S + E;  // |E| << S: fast two-sum
+    return make_float2(h, E - (h - S));
 }
 
 // the same with both operands in FP64
 template <int K>
-__device__ __forceinline__ double df_dot(const double (&a)[K], const double (&b)[K], bool &big) {
+__device__ __forceinline__ float2 df_dot(const double (&a)[K], const double (&b)[K], bool &big) {
     float ah[K], al[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) df_cut(a[r], ah[r], al[r], big);
     return df_dot<K>(ah, al, b, big);
+}
+
+// x / max(s, eps) in FP64 from the pair s = s.x + s.y and eps = eh + el, on the
+// FP32 pipe: q0 = x_hi / m_hi to single precision (the hardware reciprocal
+// estimate), then the classical correction of a double-length division
+// (Dekker): the residual x - q0 m, formed exactly to first order with the FMA
+// product q0 m_hi = p + pe (x_hi - p is exact: p is within a factor of two of
+// x_hi), divided by m_hi gives q1, and q0 + q1 is the quotient.  |q1| <= 2^-21
+// q0 and q1 carries a relative error of about 2^-22 (estimate, rounding), so
+// the quotient is within 2^-43 relative; x enters with its 48 leading bits
+// (2^-48).  One FP64 addition widens it.  Needs x = 0 or 2^-20 <= x < 2^31
+// (checked by df_check_x), eps >= 2^-43 and s < 2^66 (eight operands < 2^31 per
+// lane, up to 16 lanes), so that q0 and q1 are normal floats.
+__device__ __forceinline__ double df_divide(double x, float2 s, float eh, float el) {
+    float xh, xl;
+    bool unused = false;
+    df_cut(x, xh, xl, unused);
+    const bool use_s = (s.x - eh) + (s.y - el) >= 0.f;  // s.x - eh is exact where they are close
+    const float mh = use_s ? s.x : eh, ml = use_s ? s.y : el;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(mh));
+    const float q0 = xh * r;
+    const float p = q0 * mh;
+    const float pe = fmaf(q0, mh, -p);
+    const float res = ((xh - p) - pe) + fmaf(-q0, ml, xl);
+    return df_widen(q0) + df_widen(res * r);
+}
+
+// sets big unless x = 0 or 2^-20 <= x < 2^31 (the range df_divide handles);
+// integer operations on the bits of x >= 0
+__device__ __forceinline__ void df_check_x(double x, bool &big) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(bits >> 52);
+    big = big || (bits != 0ull && (e < 1023u - 20u || e >= 1023u + 31u));
+}
+
+// the reduce-scatter below for hi/lo float pairs (two shuffles per pair)
+template <int G, int U>
+__device__ __forceinline__ float2 group_reduce_scatter_df(float2 (&s)[U], int lane, unsigned gmask) {
+    static_assert(U <= G, "reduce-scatter needs U <= G");
+    int o = G / 2;
+#pragma unroll
+    for (int h = U / 2; h >= 1; h >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float2 send = upper ? s[i] : s[i + h];
+            const float2 keep = upper ? s[i + h] : s[i];
+            s[i] = df_add(keep, make_float2(__shfl_xor_sync(gmask, send.x, o), __shfl_xor_sync(gmask, send.y, o)));
+        }
+        o >>= 1;
+    }
+    float2 tot = s[0];
+#pragma unroll
+    for (int oo = G / (2 * U); oo > 0; oo >>= 1)
+        tot = df_add(tot, make_float2(__shfl_xor_sync(gmask, tot.x, oo), __shfl_xor_sync(gmask, tot.y, oo)));
+    return tot;
 }
 
 // On entry each of the G lanes of a group holds U partial dot products (its
@@ -669,6 +743,11 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     const T *__restrict__ Bm = reinterpret_cast<const T *>(a.B);
     T *__restrict__ out = reinterpret_cast<T *>(a.out);
     const T eps = (T)a.eps;
+    float eps_hi = 0.f, eps_lo = 0.f;  // eps as a hi/lo float pair (FP32-pipe division)
+    {
+        bool unused = false;
+        df_cut(a.eps, eps_hi, eps_lo, unused);
+    }
 
     // Contiguous run [la, lb) of the tile for this group.  Runs start on
     // multiples of U (vector loads of a batch).  With one lane per group an
@@ -855,21 +934,37 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                 T s[U];
                 bool fp64dot = true;
                 if constexpr (DFDOT) {
-                    {
-                        // <B[i_n], pi> on the FP32 pipe; each lane's partial in FP64
-                        bool big = false;
+                    // <B[i_n], pi>, the lanes' sum and x / max(s, eps) on the FP32 pipe,
+                    // unless an operand or x is outside their ranges somewhere in the group
+                    float2 s2[U];
+                    bool big = false;
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if (BREG && fast) {
-                                if constexpr (BREG) s[u] = (T)df_dot<RPL>(bhi, blo, pi[u], big);
-                            } else {
-                                T brw[RPL];
-                                load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, brw);
-                                s[u] = (T)df_dot<RPL>(brw, pi[u], big);
-                            }
+                    for (int u = 0; u < U; ++u) {
+                        df_check_x((double)xx[u], big);
+                        if (BREG && fast) {
+                            if constexpr (BREG) s2[u] = df_dot<RPL>(bhi, blo, pi[u], big);
+                        } else {
+                            T brw[RPL];
+                            load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, brw);
+                            s2[u] = df_dot<RPL>(brw, pi[u], big);
                         }
-                        if constexpr (BREG) big = big || (fast && bbig);
-                        fp64dot = __any_sync(gmask, big);
+                    }
+                    if constexpr (BREG) big = big || (fast && bbig);
+                    fp64dot = __any_sync(gmask, big);
+                    if (!fp64dot) {
+                        if constexpr (G == 1) {
+#pragma unroll
+                            for (int u = 0; u < U; ++u) v[u] = (T)df_divide((double)xx[u], s2[u], eps_hi, eps_lo);
+                        } else {
+                            const float2 tot = group_reduce_scatter_df<G, U>(s2, lane, gmask);
+                            T xm = xx[0];
+#pragma unroll
+                            for (int u = 1; u < U; ++u)
+                                if (u_mine == u) xm = xx[u];
+                            const T vm = (T)df_divide((double)xm, tot, eps_hi, eps_lo);
+#pragma unroll
+                            for (int u = 0; u < U; ++u) v[u] = __shfl_sync(gmask, vm, gbase + u * LPU);
+                        }
                     }
                 }
                 if (fp64dot) {
@@ -884,7 +979,9 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                             s[u] = dot_global<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, pi[u]);
                     }
                 }
-                if constexpr (G == 1) {
+                if (!fp64dot) {
+                    // v done on the FP32 pipe above
+                } else if constexpr (G == 1) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         if (OP == OP_PHI) {
