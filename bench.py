@@ -65,14 +65,16 @@ L2_GATHER_GBS = 7450.0
 # same dims, rank and distributions but 1e7 nonzeros (a few GB on the device, as the capture rules ask);
 # its traffic is scaled to the full tensor per mode as (bytes - io) * nnz_full / nnz + io, where io is
 # the algorithmic B read plus Phi write (2 R b_f I_n), the only part that does not grow with the
-# nonzeros.  A run in any other configuration reports traffic null; an entry is dropped when its kernel
-# changes.
+# nonzeros.  "l2_read" is lts__t_sectors_srcunit_tex_op_read.sum x 32 bytes (the L2 bytes read by L1
+# misses: the gathered factor rows the L1 did not hold) for a fused configuration.  A run in any other
+# configuration reports traffic null; an entry is dropped when its kernel changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
         {"bytes": [2667572480 + 16308736, 2667997952 + 11258880, 2641735424 + 850432], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
         {"bytes": [150059520 + 9511424, 149919744 + 6664704, 150980608 + 513792], "nnz": 10_000_000,
+         "l2_read": [45740962 * 32, 45503623 * 32, 56096494 * 32],
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
         {"bytes": [1386854912 + 11519232, 1386826496 + 8379904, 1363041024 + 544256, 1361456128 + 181248],

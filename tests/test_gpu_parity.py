@@ -775,3 +775,26 @@ def test_fp64_dot_fallbacks_match_oracle(pi_mode):
             t.set_model(lam, fs)
             want = oracle.phi(T.dims, T.idx, T.vals, fs, B, n, eps=1e-20)
             assert max_rel(t.phi(n, B=B), want) <= 1e-12, n
+
+
+@pytest.mark.parametrize("pi_mode", PI_MODES)
+def test_fp64_division_value_range_matches_oracle(pi_mode):
+    """On the FP32 pipe the FP64 form also divides x / max(s, eps); values
+    outside {0} and [2^-20, 2^31) make their group redo the batch with the
+    FP64 dot and division.  Tensor values from 1e-30 to 4e9 (exact zeros,
+    values at both edges of the range) against the oracle at the FP64 bound."""
+    T = case("c3s")
+    lam, fs = model_for(T, 32)
+    rng = np.random.default_rng(6)
+    vals = T.vals * 10.0 ** rng.uniform(-8, 6, size=T.vals.shape)
+    vals[::13] = 0.0
+    vals[1::17] = 1e-30
+    vals[2::19] = 2.0 ** -20
+    vals[3::23] = 2.0 ** 31
+    vals[4::29] = 4e9
+    vals[5::31] = 2.0 ** 31 - 2.0 ** 8
+    with cpapr.Tensor(T.dims, T.idx, vals, T.rank, pi_mode=pi_mode, fp64_dot=cpapr.CPAPR_DOT_FP32_PIPE) as t:
+        t.set_model(lam, fs)
+        for n in range(T.nmodes):
+            want = oracle.phi(T.dims, T.idx, vals, fs, fs[n] * lam[None, :], n)
+            assert max_rel(t.phi(n), want) <= 1e-12, n
