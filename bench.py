@@ -133,10 +133,10 @@ def phi_flops(N, nnz, R, materialised=False) -> float:
 
 def phi_fp64_pipe_flops(N, nnz, R, materialised=False, dot_on_fp32=True) -> float:
     """The part of phi_flops the FP64 Phi kernel runs on the FP64 pipe: with
-    the dot <B, pi> on the FP32 pipe (8 or fewer ranks per lane, eps >= 2^-43)
-    the 2R of the dot leave it, leaving the scale-add, the division and, fused,
-    the Khatri-Rao products."""
-    return phi_flops(N, nnz, R, materialised) - (nnz * 2 * R if dot_on_fp32 else 0)
+    the divisor x / max(<B, pi>, eps) on the FP32 pipe (8 or fewer ranks per
+    lane, eps >= 2^-43) the dot's 2R and the max and divide leave it, leaving
+    the scale-add and, fused, the Khatri-Rao products."""
+    return phi_flops(N, nnz, R, materialised) - (nnz * (2 * R + 2) if dot_on_fp32 else 0)
 
 
 def phi_gather_bytes(N, nnz, R, factor_bytes, materialised=False) -> float:
@@ -618,13 +618,13 @@ def roofline_for(T, inner_per_mode, stats, precision, peaks, cp, pi_modes=None, 
     if precision == cp.CPAPR_FP64:
         ach = fl64 / sec / 1e12
         dot32 = all(on32)
-        model = ("2R+2" if all(mat) else "NR+2") if dot32 else ("4R+2" if all(mat) else "(N+2)R+2")
+        model = ("2R" if all(mat) else "NR") if dot32 else ("4R+2" if all(mat) else "(N+2)R+2")
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": f"phi_tile_kernel<double> ({form})",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
                 "flop_model": f"{model} FP64 FLOPs per nonzero on the FP64 pipe"
-                              + (" (the dot's 2R run on the FP32 pipe)" if dot32 else ""),
+                              + (" (the dot's 2R and the max and divide run on the FP32 pipe)" if dot32 else ""),
                 "paper_flop_model": {"achieved": fl / sec / 1e12, "unit": "TFLOP/s",
                                      "per_nonzero": "4R+2" if all(mat) else "(N+2)R+2"}}
     else:

@@ -239,7 +239,7 @@ cpapr_status cpapr_phi(cpapr_ctx *ctx, int32_t mode, const double *B, double *ou
  * current device is restored before it returns) and synchronises the
  * context's stream before returning.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).
  * All calls share the one array and it keeps the last call's contents
  * (nothing in it needs to start at zero): calls that overlap on the GPU --
  * on other streams, contexts or host threads -- race and must be serialised

@@ -256,15 +256,17 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BatchTensor *__
         const int Rp = d.rp;
         const int64_t r0 = (int64_t)w.y * kChunkRows;
         const int64_t r1 = min(r0 + kChunkRows, d.rows);
-        // 16-byte vectors (a row is a whole number of them)
-        using V = typename Vec16<T>::type;
-        constexpr int W = Vec16<T>::n;
-        V *B = reinterpret_cast<V *>(const_cast<void *>(d.a.B));
-        const V *P = reinterpret_cast<const V *>(d.a.out);
-        if (d.Bm) {
-            for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x)
-                B[e] = master_mul(d.Bm, P[e], e);
+        if constexpr (sizeof(T) == 4) {
+            // FP32 form: on the FP64 master, in pairs (a row is a whole number of them)
+            for (int64_t e = r0 * Rp / 2 + threadIdx.x; e < r1 * Rp / 2; e += blockDim.x)
+                master_mul(reinterpret_cast<double2 *>(d.Bm), reinterpret_cast<float2 *>(const_cast<void *>(d.a.B)),
+                           reinterpret_cast<const float2 *>(d.a.out), e);
         } else {
+            // 16-byte vectors (a row is a whole number of them)
+            using V = typename Vec16<T>::type;
+            constexpr int W = Vec16<T>::n;
+            V *B = reinterpret_cast<V *>(const_cast<void *>(d.a.B));
+            const V *P = reinterpret_cast<const V *>(d.a.out);
             for (int64_t e = r0 * Rp / W + threadIdx.x; e < r1 * Rp / W; e += blockDim.x) B[e] = vmul(B[e], P[e]);
         }
     }

@@ -248,21 +248,18 @@ __device__ __forceinline__ float4 vmul(float4 a, float4 b) {
 }
 __device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 
-// FP32 form of B <- B * Phi on the FP64 master: vector e of four B entries
-// (Bm[4e .. 4e+3]) times the FP32 Phi vector p; returns the FP32 copy.
-__device__ __forceinline__ float4 master_mul(double *__restrict__ Bm, float4 p, int64_t e) {
-    double2 *b = reinterpret_cast<double2 *>(Bm) + 2 * e;
-    double2 lo = b[0], hi = b[1];
-    lo.x *= (double)p.x;
-    lo.y *= (double)p.y;
-    hi.x *= (double)p.z;
-    hi.y *= (double)p.w;
-    b[0] = lo;
-    b[1] = hi;
-    return make_float4((float)lo.x, (float)lo.y, (float)hi.x, (float)hi.y);
+// FP32 form of B <- B * Phi on the FP64 master, for the pair of entries
+// (2e, 2e + 1): the master pair times the FP32 Phi pair, and its FP32 copy
+// (a warp reads and writes 512 contiguous bytes of the master, 256 of Phi and B)
+__device__ __forceinline__ void master_mul(double2 *__restrict__ Bm, float2 *__restrict__ B,
+                                           const float2 *__restrict__ P, int64_t e) {
+    const float2 p = P[e];
+    double2 b = Bm[e];
+    b.x *= (double)p.x;
+    b.y *= (double)p.y;
+    Bm[e] = b;
+    B[e] = make_float2((float)b.x, (float)b.y);
 }
-// (never called: the FP64 form has no master)
-__device__ __forceinline__ double2 master_mul(double *__restrict__, double2 p, int64_t) { return p; }
 
 __device__ __forceinline__ unsigned long long ordered_bits(double v) {
     // v >= 0: IEEE bit patterns of non-negative doubles order like the values

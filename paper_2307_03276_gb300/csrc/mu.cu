@@ -94,16 +94,18 @@ __global__ void update_kernel(T *__restrict__ B, double *__restrict__ Bm, const 
     const int l = s_l, done = s_done;
     const double viol = s_viol;
     if (!done && !(viol < tol)) {
-        // 16-byte vectors: n is a whole number of them (rows of Rp values)
-        using V = typename Vec16<T>::type;
-        V *Bv = reinterpret_cast<V *>(B);
-        const V *Pv = reinterpret_cast<const V *>(P);
-        const int64_t nv = n / Vec16<T>::n;
-        if (Bm) {
-            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 form: on the FP64 master, in pairs (n is even: rows of Rp >= 4 values)
+            for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n / 2;
                  e += (int64_t)gridDim.x * blockDim.x)
-                Bv[e] = master_mul(Bm, Pv[e], e);
+                master_mul(reinterpret_cast<double2 *>(Bm), reinterpret_cast<float2 *>(B),
+                           reinterpret_cast<const float2 *>(P), e);
         } else {
+            // 16-byte vectors: n is a whole number of them (rows of Rp values)
+            using V = typename Vec16<T>::type;
+            V *Bv = reinterpret_cast<V *>(B);
+            const V *Pv = reinterpret_cast<const V *>(P);
+            const int64_t nv = n / Vec16<T>::n;
             for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv;
                  e += (int64_t)gridDim.x * blockDim.x)
                 Bv[e] = vmul(Bv[e], Pv[e]);

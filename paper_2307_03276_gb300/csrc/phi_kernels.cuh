@@ -120,6 +120,34 @@ template <typename T> __device__ __forceinline__ T viol_t(T b, T phi) {
     return m < T(0) ? -m : m;
 }
 
+// x >= 0 as a float hi <= x within 2^-23 relative (its leading 24 bits, by
+// integer operations); false where x is outside the float range
+__device__ __forceinline__ bool hi_of(double x, float &hi) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const uint32_t H = (uint32_t)(bits >> 32), L = (uint32_t)bits;
+    const uint32_t e = H >> 20;
+    hi = bits ? __uint_as_float(__funnelshift_l(L, H, 3) - (896u << 23)) : 0.f;
+    return bits == 0ull || (e >= 1023u - 126u && e < 1023u + 127u);
+}
+
+// The running KKT maximum k of an FP64 Phi kernel takes the exact term
+// |min(b, 1 - phi)| only where an FP32 estimate from the leading 24 bits of b
+// (b_hi) and of phi could exceed it: the estimate is within 2^-22 (1 + phi + b)
+// of the term (b_hi and phi_hi are within 2^-23 relative, 1 - phi_hi rounds
+// once, min and |.| are 1-Lipschitz), so with twice that margin no term above
+// k is skipped and the maximum stays exact.  kf is a float <= k.
+__device__ __forceinline__ bool kkt_candidate(float b_hi, double phi, float kf) {
+    float ph;
+    if (!hi_of(phi, ph)) return true;
+    const float m = fminf(b_hi, 1.f - ph);
+    return fabsf(m) + 0x1p-21f * (1.f + ph + b_hi) >= kf;
+}
+__device__ __forceinline__ float float_below(double k) {
+    float h;
+    if (hi_of(k, h)) return h;
+    return ((unsigned long long)__double_as_longlong(k) >> 52) < 1023ull ? 0.f : 3.4028234663852886e38f;
+}
+
 // x / max(s, eps) of Algorithm 2.
 // FP64: s >= 0, so the maximum is taken on the bit patterns (integer ALU,
 // not the FP64 pipe).  r0 is the hardware's approximate FP64 reciprocal of m
@@ -226,15 +254,6 @@ __device__ __forceinline__ float2 df_dot(const float (&ahi)[K], const float (&al
     const float E = C + D;
     const float h = S + E;  // |E| << S: fast two-sum
     return make_float2(h, E - (h - S));
-}
-
-// the same with both operands in FP64
-template <int K>
-__device__ __forceinline__ float2 df_dot(const double (&a)[K], const double (&b)[K], bool &big) {
-    float ah[K], al[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) df_cut(a[r], ah[r], al[r], big);
-    return df_dot<K>(ah, al, b, big);
 }
 
 // x / max(s, eps) in FP64 from the pair s = s.x + s.y and eps = eh + el, on the
@@ -646,9 +665,19 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     // the tile's first and last row in nzrow, read first so that their latency
     // passes while the block checks its state and synchronises
     int32_t k0 = 0, k1 = 0;
+    // FP64 Phi on the FP32 pipe: the KKT maximum published so far (both slots
+    // and the iteration index, read at once), which seeds the running maximum
+    constexpr bool KSEED = DF && sizeof(T) == 8 && OP == OP_PHI;
+    unsigned long long kslot0 = 0ull, kslot1 = 0ull;
+    int32_t kl = 0;
     if (threadIdx.x == 0) {
         k0 = __ldg(a.krow + t);
         k1 = __ldg(a.krow + t + 1);
+        if (KSEED && a.inner) {
+            kl = *((volatile int32_t *)&a.inner->l);
+            kslot0 = *((volatile unsigned long long *)&a.inner->kkt[0]);
+            kslot1 = *((volatile unsigned long long *)&a.inner->kkt[1]);
+        }
     }
     if (a.inner && a.inner->done) return true;
     const int nm1 = PI ? 0 : (NM1 > 0 ? NM1 : a.nm1);  // staged coordinate streams
@@ -672,7 +701,8 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     T *slot_val = reinterpret_cast<T *>(s_cnt + W);                 // [2 * NG][Rp]
     int32_t *slot_row = reinterpret_cast<int32_t *>(slot_val + 2 * NG * Rp);  // [2 * NG]
     int32_t *slot_fin = slot_row + 2 * NG;  // [2]: rows spanning tiles this block finishes
-    int32_t *s_meta = slot_fin + 2;         // [2]: s_rows index of the tile's first row; rows after it
+    int32_t *s_meta = slot_fin + 2;         // [2]: s_rows index of the tile's first row; rows after it;
+                                            // then 8 bytes: the KKT maximum published so far
     // the staged bits start at the 16-byte group holding bit p0 and run
     // through the word holding bit p1 (whether the last row goes on)
     const int64_t w0 = (p0 >> 5) & ~(int64_t)3;
@@ -697,6 +727,8 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
         stage_copy(s_rows, a.nzrow + k0a, br, bar);
         s_meta[0] = k0 - k0a;
         s_meta[1] = k1 - k0;
+        // the maximum published so far: terms below it cannot change the result
+        *reinterpret_cast<unsigned long long *>(s_meta + 2) = (kl & 1) ? kslot1 : kslot0;
     }
     const bool segmented = (OP != OP_LL) && !a.atomic;
     if (segmented) {
@@ -762,7 +794,9 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     }
     const int la = min(g * vlen, n), lb = min(la + vlen, n);
 
+    // running KKT maximum, from the one published so far (FP64 Phi on the FP32 pipe)
     T kkt = T(0);
+    if constexpr (KSEED) kkt = (T)__longlong_as_double(*reinterpret_cast<const long long *>(s_meta + 2));
     double ll = 0.0;
     // with G > 1 lanes each lane finishes one nonzero of the batch: u_mine
     constexpr int LPU = G > 1 ? G / U : 1;  // lanes per nonzero after the reduce-scatter
@@ -819,7 +853,20 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
             const bool before = first && head_open, after = last && tail_open;
             if (!before && !after) {
                 store_row<T, RPL>(out + (int64_t)frow * Rp + col0, v);
-                if (OP == OP_PHI) {
+                if (OP == OP_PHI && a.inner) {
+                    if constexpr (BREG && DFDOT) {
+                        // the exact FP64 term only where it could raise the running maximum
+                        // (flushes diverge across a warp's groups, and each FP64 warp
+                        // instruction costs the FP64 pipe the same with two lanes or 32)
+                        if (frow == brow_row && !bbig) {
+                            const float kf = float_below((double)kkt);
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r)
+                                if (kkt_candidate(bhi[r], (double)v[r], kf))
+                                    kkt = tmax(kkt, viol_t(__ldg(Bm + (int64_t)frow * Rp + col0 + r), v[r]));
+                            return;
+                        }
+                    }
                     if constexpr (BREGD) {
                         if (frow == brow_row) {
 #pragma unroll
@@ -941,13 +988,23 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         df_check_x((double)xx[u], big);
+                        // one dot for fast and slow groups alike (converged across the warp)
+                        float bh[RPL], bl[RPL];
                         if (BREG && fast) {
-                            if constexpr (BREG) s2[u] = df_dot<RPL>(bhi, blo, pi[u], big);
+                            if constexpr (BREG) {
+#pragma unroll
+                                for (int r = 0; r < RPL; ++r) {
+                                    bh[r] = bhi[r];
+                                    bl[r] = blo[r];
+                                }
+                            }
                         } else {
                             T brw[RPL];
                             load_row<T, RPL>(Bm + (int64_t)rr[u] * Rp + col0, brw);
-                            s2[u] = df_dot<RPL>(brw, pi[u], big);
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r) df_cut((double)brw[r], bh[r], bl[r], big);
                         }
+                        s2[u] = df_dot<RPL>(bh, bl, pi[u], big);
                     }
                     if constexpr (BREG) big = big || (fast && bbig);
                     fp64dot = __any_sync(gmask, big);
@@ -1033,7 +1090,31 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                     }
                 }
             }
-            if (fast) {
+            if constexpr (sizeof(T) == 8) {
+                // Row changes (slow batches only) flush the run's sum; the scale-add
+                // itself runs for every group of the warp together, fast or slow, a
+                // nonzero past the run's end adding 0 * pi: each FP64 warp
+                // instruction costs the FP64 pipe the same with two lanes or 32.
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!fast && q + u < lb && rr[u] != cur) {
+                        if (OP != OP_LL) {
+                            flush(cur, first_run, false);
+#pragma unroll
+                            for (int h = 0; h < NACC; ++h)
+#pragma unroll
+                                for (int r = 0; r < RPL; ++r) acc[h][r] = T(0);
+                        }
+                        first_run = false;
+                        cur = rr[u];
+                    }
+                    if (OP != OP_LL) {
+                        const T w = (fast || q + u < lb) ? v[u] : T(0);
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) acc[u % NACC][r] = fma(w, pi[u][r], acc[u % NACC][r]);
+                    }
+                }
+            } else if (fast) {
                 if (OP != OP_LL) {
 #pragma unroll
                     for (int u = 0; u < U; ++u)
@@ -1061,11 +1142,11 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                         }
                     }
                 }
-                if constexpr (BREG) {
-                    if (cur != brow_row) {
-                        load_brow();
-                        brow_row = cur;
-                    }
+            }
+            if constexpr (BREG) {
+                if (!fast && cur != brow_row) {
+                    load_brow();
+                    brow_row = cur;
                 }
             }
         }

@@ -102,9 +102,9 @@ def test_roofline_line_is_strict_json():
     r = bench.roofline_for(T, inner, {0: (30, 43.6)}, 0, {"hbm_gbs": 6682.5, "source": "measured"}, CP,
                            [2, 2, 2], Info())
     json.dumps(r, allow_nan=False)
-    # 8 ranks per lane: the dot runs on the FP32 pipe, 2R + 2 FP64 FLOPs per nonzero remain
-    assert r["bound"] == "alu" and r["flop_model"].startswith("2R+2 FP64 FLOPs per nonzero on the FP64 pipe")
-    flops = 30 * 1e7 * (2 * 32 + 2)
+    # 8 ranks per lane: the divisor runs on the FP32 pipe, the scale-add's 2R FP64 FLOPs per nonzero remain
+    assert r["bound"] == "alu" and r["flop_model"].startswith("2R FP64 FLOPs per nonzero on the FP64 pipe")
+    flops = 30 * 1e7 * (2 * 32)
     assert abs(r["achieved"] - flops / 43.6e-3 / 1e12) < 1e-9
     assert abs(r["paper_flop_model"]["achieved"] - 30 * 1e7 * (4 * 32 + 2) / 43.6e-3 / 1e12) < 1e-9
     assert r["traffic"] is not None and 2.6e9 < r["traffic"] < 2.8e9
