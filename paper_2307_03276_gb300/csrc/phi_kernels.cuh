@@ -1090,7 +1090,7 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
                     }
                 }
             }
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (DF && sizeof(T) == 8) {
                 // Row changes (slow batches only) flush the run's sum; the scale-add
                 // itself runs for every group of the warp together, fast or slow, a
                 // nonzero past the run's end adding 0 * pi: each FP64 warp
