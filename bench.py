@@ -70,14 +70,14 @@ L2_GATHER_GBS = 7450.0
 # configuration reports traffic null; an entry is dropped when its kernel changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        {"bytes": [2667572480 + 16308736, 2667997952 + 11258880, 2641735424 + 850432], "nnz": 10_000_000,
+        {"bytes": [2667816704 + 16342528, 2667661568 + 14832640, 2642004992 + 3737344], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
         {"bytes": [150059520 + 9511424, 149919744 + 6664704, 150980608 + 513792], "nnz": 10_000_000,
          "l2_read": [45740962 * 32, 45503623 * 32, 56096494 * 32],
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
-        {"bytes": [1386854912 + 11519232, 1386826496 + 8379904, 1363041024 + 544256, 1361456128 + 181248],
+        {"bytes": [1386872832 + 12450560, 1387290112 + 12221440, 1362819584 + 3279616, 1361475840 + 3460608],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
@@ -297,7 +297,7 @@ def _oracle_phi_rate(T, lam, fs, S, seconds, threads):
 
 def cpu_baseline(T, lam, fs, seconds: float = 10.0, sample: int = 1_000_000) -> dict:
     """The FP64 oracle as it stands on a bounded sample of the same tensor:
-    on all the host's cores (per-thread Phi copies added at the end) and,
+    on all the host's cores (each thread owns a range of Phi's rows) and,
     beside it, on one core."""
     import oracle
     oracle.build()
@@ -308,8 +308,8 @@ def cpu_baseline(T, lam, fs, seconds: float = 10.0, sample: int = 1_000_000) -> 
     vm, km, dm = _oracle_phi_rate(T, lam, fs, Sm, seconds / 2, cores)
     return {"value": vm, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"Phi^(n) over the first {Sm:,} of {T.nnz:,} nonzeros (random draw order), modes cycled, "
-                      f"{km} evaluations in {dm:.1f} s, FP64, Neumaier row sums, {cores} threads (per-thread Phi "
-                      f"copies over contiguous chunks, added in thread order)",
+                      f"{km} evaluations in {dm:.1f} s, FP64, Neumaier row sums, {cores} threads (each owns a range "
+                      f"of Phi's rows; bit-identical to one thread)",
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
                               "sample": f"Phi^(n) over the first {S1:,} nonzeros, modes cycled, {k1} evaluations "
                                         f"in {d1:.1f} s, one thread"}}
