@@ -73,8 +73,8 @@ NCU_TRAFFIC = {
         {"bytes": [2667816704 + 16342528, 2667661568 + 14832640, 2642004992 + 3737344], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
-        {"bytes": [150059520 + 9511424, 149919744 + 6664704, 150980608 + 513792], "nnz": 10_000_000,
-         "l2_read": [45740962 * 32, 45503623 * 32, 56096494 * 32],
+        {"bytes": [149920512 + 9855744, 149870848 + 6829568, 150985472 + 916480], "nnz": 10_000_000,
+         "l2_read": [46078048 * 32, 45825406 * 32, 56520460 * 32],
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
         {"bytes": [1386872832 + 12450560, 1387290112 + 12221440, 1362819584 + 3279616, 1361475840 + 3460608],
@@ -82,7 +82,7 @@ NCU_TRAFFIC = {
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f32", "materialised", (4, 4, 4, 4), (4096, 4096, 4096, 4096)):
-        {"bytes": [694901248 + 3416832, 694904832 + 191488, 682061568 + 286720, 681378304 + 224000],
+        {"bytes": [694905088 + 3333888, 694989056 + 212992, 682062336 + 261888, 681425920 + 171520],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP32 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
