@@ -68,7 +68,7 @@ cudaError_t run(const PhiArgs &a, cudaStream_t s, const cudaAccessPolicyWindow *
         // FP64 Phi with 8 or fewer ranks per lane: the launcher's choice of the
         // kernel that takes the dot on the FP32 pipe
         if constexpr (sizeof(PHI_T) == 8 && OP == OP_PHI && RPL <= 8) {
-            if (a.dfdot) return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI, true>, a, s, win);
+            if (a.dfdot) return launch<RPL>(phi_tile_kernel_df<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
         }
         return launch<RPL>(phi_tile_kernel<PHI_T, PHI_NM1, RPL, G, OP, kThreads, U, PI>, a, s, win);
     }

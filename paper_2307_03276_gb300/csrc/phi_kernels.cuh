@@ -1272,21 +1272,33 @@ __device__ __forceinline__ bool phi_tile_body(const PhiArgs &a, const int t, uns
     return true;
 }
 
-// One block per tile of one tensor.  The FP64 kernel with the divisor on the
-// FP32 pipe runs at five blocks per SM (registers held to 96, a few spilled)
-// with four or more lanes per nonzero: measured on GB300 4-6% faster on the
-// 3-way R = 32 and 5-way R = 32 and 64 tensors; with two lanes (R = 16, whose
-// 2048-nonzero stages would then take 213 KB of an SM's shared memory) it
-// was 3-4% slower, so those are held to four (128 registers).
-template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI, bool DF = false>
-__global__ void __launch_bounds__(THREADS, DF ? (G >= 4 ? 5 : 4) : 1) phi_tile_kernel(const PhiArgs a) {
+// One block per tile of one tensor.
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI>
+__global__ void __launch_bounds__(THREADS) phi_tile_kernel(const PhiArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[THREADS / 32];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) stage_barrier_init(&bar);
     __syncthreads();
     uint32_t phase = 0;
-    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI, DF>(a, blockIdx.x, smem_raw, red, &bar, phase);
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI>(a, blockIdx.x, smem_raw, red, &bar, phase);
+}
+
+// The FP64 Phi kernel with the divisor on the FP32 pipe.  With four or more
+// lanes per nonzero it runs at five blocks per SM (registers held to 96, a
+// few spilled): measured on GB300 4-6% faster on the 3-way R = 32 and 5-way
+// R = 32 and 64 tensors; with two lanes (R = 16, whose 2048-nonzero stages
+// would then take 213 KB of an SM's shared memory) it was 3-4% slower, so
+// those are held to four blocks (128 registers).
+template <typename T, int NM1, int RPL, int G, int OP, int THREADS, int U, bool PI>
+__global__ void __launch_bounds__(THREADS, G >= 4 ? 5 : 4) phi_tile_kernel_df(const PhiArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[THREADS / 32];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) stage_barrier_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    phi_tile_body<T, NM1, RPL, G, OP, THREADS, U, PI, true>(a, blockIdx.x, smem_raw, red, &bar, phase);
 }
 
 // The same with registers held to four resident blocks per SM (64 per
