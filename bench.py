@@ -70,14 +70,14 @@ L2_GATHER_GBS = 7450.0
 # configuration reports traffic null; an entry is dropped when its kernel changes.
 NCU_TRAFFIC = {
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f64", "materialised", (4, 4, 4), (1024, 1024, 1024)):
-        {"bytes": [2667917568 + 18840576, 2668117248 + 17070080, 2642238464 + 5901056], "nnz": 10_000_000,
+        {"bytes": [2668266240 + 18964736, 2667915520 + 16923904, 2642699520 + 6055680], "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-2"},
     ("c2_3way_1e5x1e5x1e3_1e7_r32", "f32", "fused", (8, 8, 8), (2048, 2048, 2048)):
         {"bytes": [149920512 + 9855744, 149870848 + 6829568, 150985472 + 916480], "nnz": 10_000_000,
          "l2_read": [46078048 * 32, 45825406 * 32, 56520460 * 32],
          "source": "ncu capture of the FP32 fused-Pi tile kernel, modes 0-2"},
     ("c3_4way_2e5x2e5x1e4x365_5e7_r16", "f64", "materialised", (2, 2, 2, 2), (2048, 2048, 2048, 2048)):
-        {"bytes": [1386904064 + 12463616, 1386850560 + 12300544, 1363127040 + 2958592, 1361444096 + 3114496],
+        {"bytes": [1386862336 + 12523776, 1386850048 + 12308224, 1362785024 + 3010048, 1361540096 + 3038976],
          "nnz": 10_000_000,
          "source": "ncu capture of the FP64 materialised-Pi tile kernel, modes 0-3, on the 4-way tensor's "
                    "1e7-nonzero copy (same dims), scaled to 5e7 nonzeros"},
