@@ -191,3 +191,48 @@ def test_float_double_conversions_by_integer_operations_are_exact():
             if np.isfinite(f) and f != 0:
                 assert widen(f) == float(f)  # to_f64 of a normal float: the df_widen bits
     assert checked > 40000
+
+
+def _hi_of(x):
+    """internal phi_kernels.cuh hi_of: the leading 24 bits of x >= 0 as a float
+    (None outside the float range)."""
+    if x == 0.0:
+        return f32(0)
+    bits = _d2u(x)
+    e = bits >> 52
+    if not (1023 - 126 <= e < 1023 + 127):
+        return None
+    H, L = bits >> 32, bits & 0xFFFFFFFF
+    return _u2f((((H << 3) | (L >> 29)) & 0xFFFFFFFF) - (896 << 23))
+
+
+def test_kkt_estimate_margin_covers_the_exact_term():
+    """The FP64 kernel takes a KKT term |min(b, 1 - phi)| in FP64 only where
+    its FP32 estimate from the leading 24 bits of b and phi, plus the margin
+    2^-21 (1 + phi_hi + b_hi), reaches the running maximum.  The estimate must
+    be within half that margin of the exact term, so that no term above the
+    maximum is skipped: checked against exact rationals over values near 1
+    (where 1 - phi cancels), tiny (b below the float range), large and zero."""
+    rng = np.random.default_rng(11)
+    cases = []
+    for _ in range(20000):
+        kind = rng.integers(5)
+        if kind == 0:
+            phi = 1.0 + rng.normal() * 10.0 ** rng.uniform(-12, -1)
+        elif kind == 1:
+            phi = 10.0 ** rng.uniform(-40, 6)
+        elif kind == 2:
+            phi = 0.0
+        else:
+            phi = rng.random() * 3
+        b = 0.0 if rng.integers(7) == 0 else 10.0 ** rng.uniform(-45, 3)
+        cases.append((abs(phi), b))
+    for phi, b in cases:
+        ph = _hi_of(phi)
+        bh, _, big = cut(b)  # the B row's hi floats of the kernel (0 below 2^-126)
+        if ph is None or big:
+            continue  # the kernel takes the exact term there
+        est = abs(min(float(bh), float(f32(f32(1.0) - ph))))
+        exact = abs(min(Fraction(b), 1 - Fraction(phi)))
+        margin = 2.0 ** -21 * (1.0 + float(ph) + float(bh))
+        assert abs(Fraction(est) - exact) <= Fraction(margin) / 2, (phi, b)
